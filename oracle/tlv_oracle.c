@@ -1,0 +1,794 @@
+/*
+ * tlv_oracle.c -- FP64 CPU oracle for the total-Lagrangian vectorial LBM
+ * (D2Q4 x 6) of Feng & Chu.
+ *
+ * TEST INFRASTRUCTURE. This file is the parity reference for the CUDA library:
+ * plain loops over the whole lattice, one phase of the paper's time step at a
+ * time (Sec. 3.7), IEEE binary64, compiled with -ffp-contract=off and no
+ * fast-math. Only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg load it. It shares no code with the CUDA sources.
+ *
+ * Readings of points the paper leaves open (each listed in the design notes):
+ *  - nodes are cell centred, so a half-way wall lies dx/2 outside the first
+ *    and last node of a non-periodic direction (Sec. 3.6);
+ *  - Neumann boundary deformation gradient F^b (Sec. 3.6.2). Two forms of
+ *    the tangential column are provided:
+ *      ORC_FB_NODE (default): F^b_iT = F_iT(x0, t^n), the value at the
+ *        boundary node itself. With the boundary manufactured solution of
+ *        Sec. 4.2 evaluated at t = 0.05 this form reproduces all six
+ *        mixed-boundary errors of Table 2 to the printed digits, so it is
+ *        taken as the form behind the paper's results;
+ *      ORC_FB_EXTRAP2: F^b_iT = 1.5 F_iT(x0) - 0.5 F_iT(x1)
+ *        + (dt/2)(1.5 dT v_i(x0) - 0.5 dT v_i(x1)), the linear extrapolation
+ *        to the wall shifted half a step by the kinematic identity of Eq. (2),
+ *        so that F^b = F(X_b, t + dt/2) + O(dt^2) as Eq. (B.20) asks.
+ *    The normal column starts from F_iN(x0, t^n) and is found by Newton on
+ *    P(F^b) N = T with a halving line search that rejects det F^b <= 0;
+ *  - boundary data (v_D, T) are sampled at t^n + dt/2 (Eq. 23); F^b uses U^n;
+ *  - no body-force term is added to the boundary sources S_d;
+ *  - at a corner each missing link belongs to exactly one edge and uses that
+ *    edge's rule; tangential derivatives are one-sided at the edge ends.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "tlv_oracle.h"
+
+/* Sec. 3.1: the D2Q4 directions (i, j) */
+static const int CI[4] = {1, 0, -1, 0};
+static const int CJ[4] = {0, 1, 0, -1};
+
+/* ======================================================================
+ * Appendix A: hyperelastic closures W(F), P(F) = dW/dF (Eqs. A.1-A.9)
+ * ====================================================================== */
+
+int orc_piola(int law, const double *p, const double F[4], double P[4])
+{
+    /* Eq. (A.1): J = det F, H = F^{-T} */
+    const double J = F[0] * F[3] - F[1] * F[2];
+    const double H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    const double trC = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
+    int m;
+    switch (law) {
+    case ORC_SVK: { /* Eq. (A.4): P = F [lambda tr(E) I + 2 mu E] */
+        const double lam = p[0], mu = p[1];
+        const double C11 = F[0] * F[0] + F[2] * F[2];
+        const double C12 = F[0] * F[1] + F[2] * F[3];
+        const double C22 = F[1] * F[1] + F[3] * F[3];
+        const double E11 = 0.5 * (C11 - 1.0), E12 = 0.5 * C12, E22 = 0.5 * (C22 - 1.0);
+        const double trE = E11 + E22;
+        const double S11 = lam * trE + 2.0 * mu * E11;
+        const double S12 = 2.0 * mu * E12;
+        const double S22 = lam * trE + 2.0 * mu * E22;
+        P[0] = F[0] * S11 + F[1] * S12;
+        P[1] = F[0] * S12 + F[1] * S22;
+        P[2] = F[2] * S11 + F[3] * S12;
+        P[3] = F[2] * S12 + F[3] * S22;
+        break;
+    }
+    case ORC_NH: { /* Eq. (A.5): P = mu (F - H) + (lambda/2)(J^2 - 1) H */
+        const double lam = p[0], mu = p[1];
+        const double a = 0.5 * lam * (J * J - 1.0);
+        for (m = 0; m < 4; ++m) P[m] = mu * (F[m] - H[m]) + a * H[m];
+        break;
+    }
+    case ORC_LOGNH: { /* Eq. (A.6): P = mu (F - H) + lambda log J H */
+        const double lam = p[0], mu = p[1];
+        const double a = lam * log(J);
+        for (m = 0; m < 4; ++m) P[m] = mu * (F[m] - H[m]) + a * H[m];
+        break;
+    }
+    case ORC_MR:
+    case ORC_YEOH:
+    case ORC_GENT: {
+        /* Eqs. (A.2)-(A.3): modified invariants and their gradients */
+        const double lam = p[0];
+        const double I1 = trC + 1.0, I2 = J * J + trC;
+        const double Jm23 = pow(J, -2.0 / 3.0), Jm43 = pow(J, -4.0 / 3.0);
+        const double A = Jm23 * I1 - 3.0;
+        double G1[4], G2[4], s1, s2 = 0.0;
+        for (m = 0; m < 4; ++m) {
+            G1[m] = Jm23 * (2.0 * F[m] - (2.0 / 3.0) * I1 * H[m]);
+            G2[m] = Jm43 * (2.0 * F[m] + (2.0 * J * J - (4.0 / 3.0) * I2) * H[m]);
+        }
+        if (law == ORC_MR) {          /* Eq. (A.7) */
+            s1 = p[1];
+            s2 = p[2];
+        } else if (law == ORC_YEOH) { /* Eq. (A.8) */
+            s1 = p[1] + 2.0 * p[2] * A + 3.0 * p[3] * A * A;
+        } else {                      /* Eq. (A.9) */
+            s1 = p[1] / (2.0 * (1.0 - A / p[2]));
+        }
+        for (m = 0; m < 4; ++m) P[m] = s1 * G1[m] + s2 * G2[m] + lam * log(J) * H[m];
+        break;
+    }
+    default:
+        return -1;
+    }
+    return (J > 0.0) ? 0 : 1;
+}
+
+double orc_energy(int law, const double *p, const double F[4])
+{
+    const double J = F[0] * F[3] - F[1] * F[2];
+    const double trC = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
+    switch (law) {
+    case ORC_SVK: {
+        const double C11 = F[0] * F[0] + F[2] * F[2];
+        const double C12 = F[0] * F[1] + F[2] * F[3];
+        const double C22 = F[1] * F[1] + F[3] * F[3];
+        const double E11 = 0.5 * (C11 - 1.0), E12 = 0.5 * C12, E22 = 0.5 * (C22 - 1.0);
+        const double trE = E11 + E22;
+        return 0.5 * p[0] * trE * trE + p[1] * (E11 * E11 + 2.0 * E12 * E12 + E22 * E22);
+    }
+    case ORC_NH:
+        return 0.5 * p[1] * (trC - 2.0 - 2.0 * log(J)) + 0.25 * p[0] * (J * J - 1.0 - 2.0 * log(J));
+    case ORC_LOGNH:
+        return 0.5 * p[1] * (trC - 2.0 - 2.0 * log(J)) + 0.5 * p[0] * log(J) * log(J);
+    case ORC_MR:
+    case ORC_YEOH:
+    case ORC_GENT: {
+        const double I1 = trC + 1.0, I2 = J * J + trC;
+        const double A = pow(J, -2.0 / 3.0) * I1 - 3.0;
+        const double vol = 0.5 * p[0] * log(J) * log(J);
+        if (law == ORC_MR) return p[1] * A + p[2] * (pow(J, -4.0 / 3.0) * I2 - 3.0) + vol;
+        if (law == ORC_YEOH) return p[1] * A + p[2] * A * A + p[3] * A * A * A + vol;
+        return -0.5 * p[1] * p[2] * log(1.0 - A / p[2]) + vol;
+    }
+    default:
+        return NAN;
+    }
+}
+
+/* Complex-argument copy of orc_piola (same formulas). Used only to obtain the
+ * tangent C = dP/dF of Eq. (4) by the complex-step derivative
+ * dP/dF_kB = Im P(F + i h e_kB) / h (Squire & Trapp 1998), exact to rounding. */
+static int piola_c(int law, const double *p, const double complex F[4], double complex P[4])
+{
+    const double complex J = F[0] * F[3] - F[1] * F[2];
+    const double complex H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    const double complex trC = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
+    int m;
+    switch (law) {
+    case ORC_SVK: {
+        const double lam = p[0], mu = p[1];
+        const double complex C11 = F[0] * F[0] + F[2] * F[2];
+        const double complex C12 = F[0] * F[1] + F[2] * F[3];
+        const double complex C22 = F[1] * F[1] + F[3] * F[3];
+        const double complex E11 = 0.5 * (C11 - 1.0), E12 = 0.5 * C12, E22 = 0.5 * (C22 - 1.0);
+        const double complex trE = E11 + E22;
+        const double complex S11 = lam * trE + 2.0 * mu * E11;
+        const double complex S12 = 2.0 * mu * E12;
+        const double complex S22 = lam * trE + 2.0 * mu * E22;
+        P[0] = F[0] * S11 + F[1] * S12;
+        P[1] = F[0] * S12 + F[1] * S22;
+        P[2] = F[2] * S11 + F[3] * S12;
+        P[3] = F[2] * S12 + F[3] * S22;
+        break;
+    }
+    case ORC_NH: {
+        const double complex a = 0.5 * p[0] * (J * J - 1.0);
+        for (m = 0; m < 4; ++m) P[m] = p[1] * (F[m] - H[m]) + a * H[m];
+        break;
+    }
+    case ORC_LOGNH: {
+        const double complex a = p[0] * clog(J);
+        for (m = 0; m < 4; ++m) P[m] = p[1] * (F[m] - H[m]) + a * H[m];
+        break;
+    }
+    case ORC_MR:
+    case ORC_YEOH:
+    case ORC_GENT: {
+        const double complex I1 = trC + 1.0, I2 = J * J + trC;
+        const double complex Jm23 = cexp((-2.0 / 3.0) * clog(J));
+        const double complex Jm43 = cexp((-4.0 / 3.0) * clog(J));
+        const double complex A = Jm23 * I1 - 3.0;
+        double complex G1[4], G2[4], s1, s2 = 0.0;
+        for (m = 0; m < 4; ++m) {
+            G1[m] = Jm23 * (2.0 * F[m] - (2.0 / 3.0) * I1 * H[m]);
+            G2[m] = Jm43 * (2.0 * F[m] + (2.0 * J * J - (4.0 / 3.0) * I2) * H[m]);
+        }
+        if (law == ORC_MR) {
+            s1 = p[1];
+            s2 = p[2];
+        } else if (law == ORC_YEOH) {
+            s1 = p[1] + 2.0 * p[2] * A + 3.0 * p[3] * A * A;
+        } else {
+            s1 = p[1] / (2.0 * (1.0 - A / p[2]));
+        }
+        for (m = 0; m < 4; ++m) P[m] = s1 * G1[m] + s2 * G2[m] + p[0] * clog(J) * H[m];
+        break;
+    }
+    default:
+        return -1;
+    }
+    return 0;
+}
+
+int orc_piola_cplx(int law, const double *prm, const double Fre[4], const double Fim[4],
+                   double Pre[4], double Pim[4])
+{
+    double complex F[4], P[4];
+    int m, rc;
+    for (m = 0; m < 4; ++m) F[m] = Fre[m] + Fim[m] * I;
+    rc = piola_c(law, prm, F, P);
+    for (m = 0; m < 4; ++m) {
+        Pre[m] = creal(P[m]);
+        Pim[m] = cimag(P[m]);
+    }
+    return rc;
+}
+
+/* Eq. (4): C_iAkB = dP_iA / dF_kB, stored at [(i*2+A)*4 + (k*2+B)] */
+int orc_tangent(int law, const double *prm, const double F[4], double C[16])
+{
+    const double h = 1e-30;
+    int col, m;
+    for (col = 0; col < 4; ++col) {
+        double complex Fc[4], Pc[4];
+        for (m = 0; m < 4; ++m) Fc[m] = F[m];
+        Fc[col] += h * I;
+        if (piola_c(law, prm, Fc, Pc) != 0) return -1;
+        for (m = 0; m < 4; ++m) C[m * 4 + col] = cimag(Pc[m]) / h;
+    }
+    return 0;
+}
+
+/* ======================================================================
+ * Sec. 2.4 and 3.2: fluxes and moment-matched equilibrium
+ * ====================================================================== */
+
+/* Eq. (7): Phi_X = (-P11, -P21, -v1, 0, -v2, 0), Phi_Y = (-P12, -P22, 0, -v1, 0, -v2) */
+void orc_flux(const double U[6], const double P[4], double PhiX[6], double PhiY[6])
+{
+    PhiX[0] = -P[0]; PhiX[1] = -P[2]; PhiX[2] = -U[0]; PhiX[3] = 0.0; PhiX[4] = -U[1]; PhiX[5] = 0.0;
+    PhiY[0] = -P[1]; PhiY[1] = -P[3]; PhiY[2] = 0.0; PhiY[3] = -U[0]; PhiY[4] = 0.0; PhiY[5] = -U[1];
+}
+
+/* Eq. (12): f^eq_ij = (1/4) [ U + (2/c) (i Phi_X + j Phi_Y) ], stored feq[q*6 + k] */
+void orc_feq(const double U[6], const double P[4], double c, double feq[24])
+{
+    double PhiX[6], PhiY[6];
+    int q, k;
+    orc_flux(U, P, PhiX, PhiY);
+    for (q = 0; q < 4; ++q)
+        for (k = 0; k < 6; ++k)
+            feq[q * 6 + k] = 0.25 * (U[k] + (2.0 / c) * (CI[q] * PhiX[k] + CJ[q] * PhiY[k]));
+}
+
+/* boundary-data time functions g(t) (shapes of Eqs. 33, 35 and Sec. 5.4) */
+double orc_timefn(int kind, const double *tp, double t)
+{
+    const double pi = 3.14159265358979323846;
+    switch (kind) {
+    case ORC_T_CONST:
+        return 1.0;
+    case ORC_T_LINEAR_RAMP:
+        return (t < tp[0]) ? t / tp[0] : 1.0;
+    case ORC_T_SIN2_RAMP: {
+        const double s = sin(pi * t / (2.0 * tp[0]));
+        return (t < tp[0]) ? s * s : 1.0;
+    }
+    case ORC_T_SIN_PULSE:
+        return (t < tp[0]) ? sin(pi * t / tp[0]) : 0.0;
+    case ORC_T_RICKER: { /* tp = {s, t0, t_end}; Ricker pulse of Sec. 5.4 per unit p0 */
+        const double z = (t - tp[1]) / tp[0];
+        if (t > tp[2]) return 0.0;
+        return 2.0 / (sqrt(3.0 * tp[0]) * pow(pi, 0.25)) * (1.0 - z * z) * exp(-0.5 * z * z);
+    }
+    default:
+        return NAN;
+    }
+}
+
+/* ======================================================================
+ * The lattice
+ * ====================================================================== */
+
+typedef struct {
+    int kind, timefn;
+    double value[2], tp[4];
+    double *profile; /* edge length, or NULL */
+    double *data;    /* 2 x edge length, or NULL */
+} orc_edge;
+
+struct orc {
+    int nx, ny;
+    long N;
+    double dx, c, omega, dt;
+    int law;
+    double prm[8];
+    double b[2];
+    double *bfield; /* 2N or NULL */
+    orc_edge e[4];
+    double *f;      /* pre-collision populations f^n, [q*6+k][n] */
+    double *fs;     /* post-collision populations f*^n           */
+    double *U;      /* recovered state U^n of the current step    */
+    double *ustar;  /* displacement accumulator u*^n, [2][n]      */
+    long step;
+    int status, ready, fb_mode;
+};
+
+static long nid(const orc *o, int ix, int iy) { return (long)iy * o->nx + ix; }
+static int edge_len(const orc *o, int e) { return (e == ORC_LEFT || e == ORC_RIGHT) ? o->ny : o->nx; }
+static int xper(const orc *o) { return o->e[ORC_LEFT].kind == ORC_PERIODIC; }
+static int yper(const orc *o) { return o->e[ORC_BOTTOM].kind == ORC_PERIODIC; }
+static double bforce(const orc *o, int comp, long n) { return o->bfield ? o->bfield[comp * o->N + n] : o->b[comp]; }
+
+orc *orc_new(int nx, int ny, double dx, double c, double omega)
+{
+    orc *o;
+    int e;
+    if (nx < 1 || ny < 1 || !(dx > 0.0) || !(c > 0.0) || !(omega > 0.0) || !(omega <= 2.0)) return NULL;
+    o = (orc *)calloc(1, sizeof(orc));
+    if (!o) return NULL;
+    o->nx = nx;
+    o->ny = ny;
+    o->N = (long)nx * ny;
+    o->dx = dx;
+    o->c = c;
+    o->omega = omega;
+    o->dt = dx / c; /* Sec. 3.1: c = dx / dt */
+    o->law = -1;
+    for (e = 0; e < 4; ++e) o->e[e].kind = ORC_PERIODIC;
+    o->f = (double *)calloc((size_t)24 * o->N, sizeof(double));
+    o->fs = (double *)calloc((size_t)24 * o->N, sizeof(double));
+    o->U = (double *)calloc((size_t)6 * o->N, sizeof(double));
+    o->ustar = (double *)calloc((size_t)2 * o->N, sizeof(double));
+    if (!o->f || !o->fs || !o->U || !o->ustar) {
+        orc_free(o);
+        return NULL;
+    }
+    return o;
+}
+
+void orc_free(orc *o)
+{
+    int e;
+    if (!o) return;
+    for (e = 0; e < 4; ++e) {
+        free(o->e[e].profile);
+        free(o->e[e].data);
+    }
+    free(o->bfield);
+    free(o->f);
+    free(o->fs);
+    free(o->U);
+    free(o->ustar);
+    free(o);
+}
+
+int orc_set_law(orc *o, int law, const double *prm, int nprm)
+{
+    int i;
+    if (law < ORC_SVK || law > ORC_GENT || nprm < 2 || nprm > 8) return -1;
+    o->law = law;
+    for (i = 0; i < 8; ++i) o->prm[i] = (i < nprm) ? prm[i] : 0.0;
+    return 0;
+}
+
+int orc_set_fb_mode(orc *o, int mode)
+{
+    if (mode != ORC_FB_NODE && mode != ORC_FB_EXTRAP2) return -1;
+    o->fb_mode = mode;
+    return 0;
+}
+
+void orc_set_body_force(orc *o, double b1, double b2)
+{
+    o->b[0] = b1;
+    o->b[1] = b2;
+}
+
+void orc_set_body_force_field(orc *o, const double *b2N)
+{
+    free(o->bfield);
+    o->bfield = NULL;
+    if (b2N) {
+        o->bfield = (double *)malloc((size_t)2 * o->N * sizeof(double));
+        memcpy(o->bfield, b2N, (size_t)2 * o->N * sizeof(double));
+    }
+}
+
+int orc_set_edge(orc *o, int e, int kind, const double value[2], int timefn, const double tp[4],
+                 const double *profile)
+{
+    orc_edge *E;
+    int len, i;
+    if (e < 0 || e > 3 || kind < ORC_PERIODIC || kind > ORC_TRACTION) return -1;
+    E = &o->e[e];
+    len = edge_len(o, e);
+    E->kind = kind;
+    E->timefn = timefn;
+    E->value[0] = value ? value[0] : 0.0;
+    E->value[1] = value ? value[1] : 0.0;
+    for (i = 0; i < 4; ++i) E->tp[i] = tp ? tp[i] : 0.0;
+    free(E->profile);
+    E->profile = NULL;
+    if (profile) {
+        E->profile = (double *)malloc((size_t)len * sizeof(double));
+        memcpy(E->profile, profile, (size_t)len * sizeof(double));
+    }
+    return 0;
+}
+
+int orc_set_edge_data(orc *o, int e, const double *vals)
+{
+    orc_edge *E;
+    int len;
+    if (e < 0 || e > 3) return -1;
+    E = &o->e[e];
+    len = edge_len(o, e);
+    free(E->data);
+    E->data = NULL;
+    if (vals) {
+        E->data = (double *)malloc((size_t)2 * len * sizeof(double));
+        memcpy(E->data, vals, (size_t)2 * len * sizeof(double));
+    }
+    return 0;
+}
+
+/* second-order difference of field a (one component, N values) along x or y
+ * at node (ix, iy): central inside, wrap-around when that direction is
+ * periodic, one-sided three-point stencil at a non-periodic end (Sec. 3.4) */
+static double fd(const orc *o, const double *a, int ix, int iy, int dir)
+{
+    const int n = dir == 0 ? o->nx : o->ny;
+    const int i = dir == 0 ? ix : iy;
+    const int per = dir == 0 ? xper(o) : yper(o);
+#define AT(j) (dir == 0 ? a[nid(o, (j), iy)] : a[nid(o, ix, (j))])
+    if (per) return (AT((i + 1) % n) - AT((i - 1 + n) % n)) / (2.0 * o->dx);
+    if (i == 0) return (-3.0 * AT(0) + 4.0 * AT(1) - AT(2)) / (2.0 * o->dx);
+    if (i == n - 1) return (3.0 * AT(n - 1) - 4.0 * AT(n - 2) + AT(n - 3)) / (2.0 * o->dx);
+    return (AT(i + 1) - AT(i - 1)) / (2.0 * o->dx);
+#undef AT
+}
+
+static int check_edges(const orc *o)
+{
+    int e;
+    if ((o->e[ORC_LEFT].kind == ORC_PERIODIC) != (o->e[ORC_RIGHT].kind == ORC_PERIODIC)) return -2;
+    if ((o->e[ORC_BOTTOM].kind == ORC_PERIODIC) != (o->e[ORC_TOP].kind == ORC_PERIODIC)) return -2;
+    if (!xper(o) && o->nx < 3) return -3;
+    if (!yper(o) && o->ny < 3) return -3;
+    for (e = 0; e < 4; ++e)
+        if (o->e[e].kind == ORC_TRACTION && edge_len(o, e) < 3) return -3;
+    return 0;
+}
+
+/* Sec. 3.4, Eqs. (16)-(21): f_q(X,0) = f^eq(U0) - (dt/2) D_q f^eq(U0) */
+int orc_init(orc *o, const double *U0, const double *u0, int order, const double *dUdX,
+             const double *dUdY)
+{
+    const long N = o->N;
+    const double c = o->c, dt = o->dt;
+    int ix, iy, q, k, m, mm;
+    int rc = check_edges(o);
+    if (rc) return rc;
+    if (o->law < 0) return -4;
+    if (order != 0 && order != 2) return -5;
+    o->status = 0;
+    for (iy = 0; iy < o->ny; ++iy)
+        for (ix = 0; ix < o->nx; ++ix) {
+            const long n = nid(o, ix, iy);
+            double U[6], F[4], P[4], feq[24];
+            for (k = 0; k < 6; ++k) U[k] = U0[k * N + n];
+            for (m = 0; m < 4; ++m) F[m] = U[2 + m];
+            if (orc_piola(o->law, o->prm, F, P) != 0) o->status |= ORC_BAD_J;
+            orc_feq(U, P, c, feq);
+            for (q = 0; q < 4; ++q)
+                for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = feq[q * 6 + k];
+            if (order == 2) {
+                double gX[6], gY[6], Ct[16], dPX[4], dPY[4];
+                const double b1 = bforce(o, 0, n), b2 = bforce(o, 1, n);
+                for (k = 0; k < 6; ++k) {
+                    gX[k] = dUdX ? dUdX[k * N + n] : fd(o, U0 + k * N, ix, iy, 0);
+                    gY[k] = dUdY ? dUdY[k * N + n] : fd(o, U0 + k * N, ix, iy, 1);
+                }
+                orc_tangent(o->law, o->prm, F, Ct);
+                /* d_alpha P_iA = C_iAkB d_alpha F_kB (text after Eq. 18) */
+                for (m = 0; m < 4; ++m) {
+                    dPX[m] = 0.0;
+                    dPY[m] = 0.0;
+                    for (mm = 0; mm < 4; ++mm) {
+                        dPX[m] += Ct[m * 4 + mm] * gX[2 + mm];
+                        dPY[m] += Ct[m * 4 + mm] * gY[2 + mm];
+                    }
+                }
+                for (q = 0; q < 4; ++q) {
+                    const double i = CI[q], j = CJ[q];
+                    double Z[6], dP[4], D[6];
+                    /* Eq. (18) */
+                    Z[0] = b1 + dPX[0] + dPY[1] + c * i * gX[0] + c * j * gY[0];
+                    Z[1] = b2 + dPX[2] + dPY[3] + c * i * gX[1] + c * j * gY[1];
+                    Z[2] = gX[0] + c * i * gX[2] + c * j * gY[2];
+                    Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
+                    Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
+                    Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
+                    /* Eqs. (19)-(20): delta P^q = C : Z_F */
+                    for (m = 0; m < 4; ++m) {
+                        dP[m] = 0.0;
+                        for (mm = 0; mm < 4; ++mm) dP[m] += Ct[m * 4 + mm] * Z[2 + mm];
+                    }
+                    /* Eq. (21) */
+                    D[0] = 0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1]));
+                    D[1] = 0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3]));
+                    D[2] = 0.25 * (Z[2] - (2.0 * i / c) * Z[0]);
+                    D[3] = 0.25 * (Z[3] - (2.0 * j / c) * Z[0]);
+                    D[4] = 0.25 * (Z[4] - (2.0 * i / c) * Z[1]);
+                    D[5] = 0.25 * (Z[5] - (2.0 * j / c) * Z[1]);
+                    for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] -= 0.5 * dt * D[k];
+                }
+            }
+            /* Sec. 3.5: u*^0 = u0 - (dt/2) v0 */
+            for (k = 0; k < 2; ++k) o->ustar[k * N + n] = (u0 ? u0[k * N + n] : 0.0) - 0.5 * dt * U[k];
+        }
+    o->step = 0;
+    o->ready = 1;
+    return 0;
+}
+
+/* node index of the node in layer L (0 = on the edge) at position s along edge e */
+static long edge_node(const orc *o, int e, int L, int s)
+{
+    switch (e) {
+    case ORC_LEFT: return nid(o, L, s);
+    case ORC_RIGHT: return nid(o, o->nx - 1 - L, s);
+    case ORC_BOTTOM: return nid(o, s, L);
+    default: return nid(o, s, o->ny - 1 - L);
+    }
+}
+
+/* derivative of state component comp of U^n along edge e (the tangential
+ * material direction), in layer L at position s */
+static double dT(const orc *o, int e, int L, int s, int comp)
+{
+    const int len = edge_len(o, e);
+    const int per = (e == ORC_LEFT || e == ORC_RIGHT) ? yper(o) : xper(o);
+    const double *a = o->U + (long)comp * o->N;
+#define AV(p) a[edge_node(o, e, L, (p))]
+    if (per) return (AV((s + 1) % len) - AV((s - 1 + len) % len)) / (2.0 * o->dx);
+    if (s == 0) return (-3.0 * AV(0) + 4.0 * AV(1) - AV(2)) / (2.0 * o->dx);
+    if (s == len - 1) return (3.0 * AV(len - 1) - 4.0 * AV(len - 2) + AV(len - 3)) / (2.0 * o->dx);
+    return (AV(s + 1) - AV(s - 1)) / (2.0 * o->dx);
+#undef AV
+}
+
+/* r_i = P_iA(F) N_A - T_i on an edge whose normal is material direction a
+ * with sign Na */
+static void traction_residual(const orc *o, const double F[4], int a, double Na, const double T[2],
+                              double r[2])
+{
+    double P[4];
+    orc_piola(o->law, o->prm, F, P);
+    r[0] = Na * P[0 * 2 + a] - T[0];
+    r[1] = Na * P[1 * 2 + a] - T[1];
+}
+
+/* Sec. 3.6.2: boundary deformation gradient F^b for a traction edge */
+static int boundary_F(orc *o, int e, int s, const double T[2], double Fb[4])
+{
+    const int a = (e == ORC_LEFT || e == ORC_RIGHT) ? 0 : 1; /* normal material index   */
+    const int tc = 1 - a;                                    /* tangential column index */
+    const double Na = (e == ORC_LEFT || e == ORC_BOTTOM) ? -1.0 : 1.0;
+    const long n0 = edge_node(o, e, 0, s), n1 = (o->fb_mode == ORC_FB_EXTRAP2) ? edge_node(o, e, 1, s) : n0;
+    const double tmax = fmax(fabs(T[0]), fabs(T[1]));
+    const double tol = 1e-13 * (tmax > 1.0 ? tmax : 1.0);
+    double r[2];
+    int i, it, ls;
+    for (i = 0; i < 2; ++i) {
+        const double F0t = o->U[(2 + i * 2 + tc) * o->N + n0];
+        if (o->fb_mode == ORC_FB_EXTRAP2) {
+            const double F1t = o->U[(2 + i * 2 + tc) * o->N + n1];
+            const double dv0 = dT(o, e, 0, s, i), dv1 = dT(o, e, 1, s, i);
+            Fb[i * 2 + tc] = 1.5 * F0t - 0.5 * F1t + 0.5 * o->dt * (1.5 * dv0 - 0.5 * dv1);
+        } else {
+            Fb[i * 2 + tc] = F0t;
+        }
+        Fb[i * 2 + a] = o->U[(2 + i * 2 + a) * o->N + n0]; /* Newton starting point */
+    }
+    traction_residual(o, Fb, a, Na, T, r);
+    for (it = 0; it < 20; ++it) {
+        double Ct[16], Jac[4], det, d0, d1, rn, alpha = 1.0;
+        int accepted = 0;
+        if (fmax(fabs(r[0]), fabs(r[1])) <= tol) return 0;
+        orc_tangent(o->law, o->prm, Fb, Ct);
+        /* d r_i / d F_ka = Na C_iaka */
+        for (i = 0; i < 2; ++i) {
+            Jac[i * 2 + 0] = Na * Ct[(i * 2 + a) * 4 + (0 * 2 + a)];
+            Jac[i * 2 + 1] = Na * Ct[(i * 2 + a) * 4 + (1 * 2 + a)];
+        }
+        det = Jac[0] * Jac[3] - Jac[1] * Jac[2];
+        d0 = -(Jac[3] * r[0] - Jac[1] * r[1]) / det;
+        d1 = -(-Jac[2] * r[0] + Jac[0] * r[1]) / det;
+        rn = hypot(r[0], r[1]);
+        for (ls = 0; ls <= 10; ++ls) {
+            double Ft[4], rt[2];
+            memcpy(Ft, Fb, sizeof Ft);
+            Ft[0 * 2 + a] += alpha * d0;
+            Ft[1 * 2 + a] += alpha * d1;
+            if (Ft[0] * Ft[3] - Ft[1] * Ft[2] > 0.0) {
+                traction_residual(o, Ft, a, Na, T, rt);
+                if (hypot(rt[0], rt[1]) < rn) {
+                    memcpy(Fb, Ft, sizeof Ft);
+                    r[0] = rt[0];
+                    r[1] = rt[1];
+                    accepted = 1;
+                    break;
+                }
+            }
+            alpha *= 0.5;
+        }
+        if (!accepted) break;
+    }
+    return (fmax(fabs(r[0]), fabs(r[1])) <= tol) ? 0 : -1;
+}
+
+/* edge data at t^n + dt/2 for position s */
+static void edge_value(const orc *o, int e, int s, double t_half, double val[2])
+{
+    const orc_edge *E = &o->e[e];
+    const int len = edge_len(o, e);
+    if (E->data) {
+        val[0] = E->data[s];
+        val[1] = E->data[len + s];
+    } else {
+        const double g = orc_timefn(E->timefn, E->tp, t_half) * (E->profile ? E->profile[s] : 1.0);
+        val[0] = E->value[0] * g;
+        val[1] = E->value[1] * g;
+    }
+}
+
+int orc_step(orc *o, int nsteps)
+{
+    const long N = o->N;
+    const double c = o->c, dt = o->dt, w = o->omega;
+    int s, q, k, ix, iy, e;
+    if (!o->ready) return -1;
+    for (s = 0; s < nsteps; ++s) {
+        const double t = o->step * dt;
+        long n;
+        /* 1. state recovery, Eq. (10): U^n = sum_q f_q + (dt/2) B */
+        for (n = 0; n < N; ++n)
+            for (k = 0; k < 6; ++k) {
+                double sum = 0.0;
+                for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
+                if (k < 2) sum += 0.5 * dt * bforce(o, k, n);
+                o->U[k * N + n] = sum;
+            }
+        /* 2-3. P(F^n), fluxes, equilibrium and BGK collision with the
+         * trapezoidal source, Eq. (14) with w_ij = 1/8 */
+        for (n = 0; n < N; ++n) {
+            double U[6], F[4], P[4], feq[24];
+            for (k = 0; k < 6; ++k) U[k] = o->U[k * N + n];
+            for (k = 0; k < 4; ++k) F[k] = U[2 + k];
+            if (orc_piola(o->law, o->prm, F, P) != 0) o->status |= ORC_BAD_J;
+            for (k = 0; k < 6; ++k)
+                if (!isfinite(U[k])) o->status |= ORC_NONFINITE;
+            orc_feq(U, P, c, feq);
+            for (q = 0; q < 4; ++q)
+                for (k = 0; k < 6; ++k) {
+                    const long idx = (long)(q * 6 + k) * N + n;
+                    const double Bk = (k < 2) ? bforce(o, k, n) : 0.0;
+                    o->fs[idx] = o->f[idx] + w * (feq[q * 6 + k] - o->f[idx]) + dt * (2.0 - w) * 0.125 * Bk;
+                }
+        }
+        /* 4. streaming, Eq. (15): f_q(X + c_q dt) = f*_q(X); links that leave a
+         * non-periodic domain are dropped and rebuilt in phase 5 */
+        for (n = 0; n < 24 * N; ++n) o->f[n] = NAN;
+        for (iy = 0; iy < o->ny; ++iy)
+            for (ix = 0; ix < o->nx; ++ix)
+                for (q = 0; q < 4; ++q) {
+                    int tx = ix + CI[q], ty = iy + CJ[q];
+                    if (tx < 0 || tx >= o->nx) {
+                        if (!xper(o)) continue;
+                        tx = (tx + o->nx) % o->nx;
+                    }
+                    if (ty < 0 || ty >= o->ny) {
+                        if (!yper(o)) continue;
+                        ty = (ty + o->ny) % o->ny;
+                    }
+                    for (k = 0; k < 6; ++k)
+                        o->f[(long)(q * 6 + k) * N + nid(o, tx, ty)] = o->fs[(long)(q * 6 + k) * N + nid(o, ix, iy)];
+                }
+        /* 5. half-way reconstruction of the missing incoming populations,
+         * Eq. (23): f_d(t+dt) = D f*_{-d}(t) + S_d(t + dt/2), d = -N */
+        for (e = 0; e < 4; ++e) {
+            const orc_edge *E = &o->e[e];
+            const int len = edge_len(o, e);
+            /* missing direction d and its opposite -d = N, and the normal N */
+            static const int dmiss[4] = {0, 2, 1, 3}, dout[4] = {2, 0, 3, 1};
+            static const double NX[4] = {-1, 1, 0, 0}, NY[4] = {0, 0, -1, 1};
+            int p;
+            if (E->kind == ORC_PERIODIC) continue;
+            for (p = 0; p < len; ++p) {
+                const long nb = edge_node(o, e, 0, p);
+                double val[2], D[6], S[6];
+                edge_value(o, e, p, t + 0.5 * dt, val);
+                if (E->kind == ORC_VELOCITY) {
+                    /* Eq. (24) */
+                    D[0] = -1; D[1] = -1; D[2] = 1; D[3] = 1; D[4] = 1; D[5] = 1;
+                    S[0] = 0.5 * val[0];
+                    S[1] = 0.5 * val[1];
+                    S[2] = NX[e] * val[0] / c;
+                    S[3] = NY[e] * val[0] / c;
+                    S[4] = NX[e] * val[1] / c;
+                    S[5] = NY[e] * val[1] / c;
+                } else {
+                    /* Eq. (25) with the boundary deformation gradient F^b */
+                    double Fb[4];
+                    if (boundary_F(o, e, p, val, Fb) != 0) o->status |= ORC_NEWTON_FAIL;
+                    D[0] = 1; D[1] = 1; D[2] = -1; D[3] = -1; D[4] = -1; D[5] = -1;
+                    S[0] = val[0] / c;
+                    S[1] = val[1] / c;
+                    for (k = 0; k < 4; ++k) S[2 + k] = 0.5 * Fb[k];
+                }
+                for (k = 0; k < 6; ++k)
+                    o->f[(long)(dmiss[e] * 6 + k) * N + nb] = D[k] * o->fs[(long)(dout[e] * 6 + k) * N + nb] + S[k];
+            }
+        }
+        /* 6. displacement quadrature, Eq. (22):
+         * u^n = u*^n + (dt/2) v^n, u*^{n+1} = u^n + (dt/2) v^n */
+        for (n = 0; n < N; ++n)
+            for (k = 0; k < 2; ++k) {
+                const double un = o->ustar[k * N + n] + 0.5 * dt * o->U[k * N + n];
+                o->ustar[k * N + n] = un + 0.5 * dt * o->U[k * N + n];
+            }
+        o->step += 1;
+    }
+    return 0;
+}
+
+/* U^n = sum_q f_q^n + (dt/2) B(t^n), P(F^n) and sigma = J^{-1} P F^T (Sec. 3.5) */
+void orc_state(const orc *o, double *U, double *P, double *sigma)
+{
+    const long N = o->N;
+    long n;
+    int q, k;
+    for (n = 0; n < N; ++n) {
+        double u6[6], F[4], Pn[4], J;
+        for (k = 0; k < 6; ++k) {
+            double sum = 0.0;
+            for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
+            if (k < 2) sum += 0.5 * o->dt * bforce(o, k, n);
+            u6[k] = sum;
+            if (U) U[k * N + n] = sum;
+        }
+        for (k = 0; k < 4; ++k) F[k] = u6[2 + k];
+        orc_piola(o->law, o->prm, F, Pn);
+        if (P)
+            for (k = 0; k < 4; ++k) P[k * N + n] = Pn[k];
+        if (sigma) {
+            J = F[0] * F[3] - F[1] * F[2];
+            /* sigma_ij = J^{-1} P_iA F_jA */
+            sigma[0 * N + n] = (Pn[0] * F[0] + Pn[1] * F[1]) / J;
+            sigma[1 * N + n] = (Pn[0] * F[2] + Pn[1] * F[3]) / J;
+            sigma[2 * N + n] = (Pn[2] * F[0] + Pn[3] * F[1]) / J;
+            sigma[3 * N + n] = (Pn[2] * F[2] + Pn[3] * F[3]) / J;
+        }
+    }
+}
+
+/* u^n = u*^n + (dt/2) v^n, Eq. (22) */
+void orc_displacement(const orc *o, double *u)
+{
+    const long N = o->N;
+    long n;
+    int q, k;
+    for (n = 0; n < N; ++n)
+        for (k = 0; k < 2; ++k) {
+            double v = 0.0;
+            for (q = 0; q < 4; ++q) v += o->f[(long)(q * 6 + k) * N + n];
+            v += 0.5 * o->dt * bforce(o, k, n);
+            u[k * N + n] = o->ustar[k * N + n] + 0.5 * o->dt * v;
+        }
+}
+
+void orc_populations(const orc *o, double *f) { memcpy(f, o->f, (size_t)24 * o->N * sizeof(double)); }
+void orc_set_populations(orc *o, const double *f) { memcpy(o->f, f, (size_t)24 * o->N * sizeof(double)); }
+int orc_status(const orc *o) { return o->status; }
+long orc_step_count(const orc *o) { return o->step; }
+double orc_time(const orc *o) { return o->step * o->dt; }
+double orc_dt(const orc *o) { return o->dt; }
