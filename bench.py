@@ -1,0 +1,368 @@
+"""Throughput benchmark of the fused collide-stream step.
+
+Workload (one "step" = one time step of the whole path over the lattice):
+a 4096 x 2048 clamped specimen -- clamped left edge, traction-free top and
+bottom, traction ramp (0.3 mu sin^2) on the right edge, NH lambda = 2, mu = 1,
+body force (0, -1e-6), c = 5, omega = 1.95 -- with FP32 populations and an FP64
+displacement accumulator. Every step runs the edge kernel (velocity and
+traction reconstruction with the Newton solve) and the fused bulk kernel.
+
+Reported (one JSON line on rank 0):
+  value     MLUPS with the state resident in HBM, timed with CUDA events on
+            the library's stream over exactly --steps steps;
+  e2e       MLUPS through the public C ABI with host buffers: initial state
+            copied in from pinned memory, displacement copied out every 1000
+            steps and the final state at the end, all inside the timed region;
+  roofline  the bulk kernel's algorithmic bytes per launch (224 B per node)
+            over its mean event-timed launch duration, against the measured
+            HBM copy bandwidth;
+  forms     the same step stored in FP64 and the 8192^2 periodic workload;
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (512 x 256 scaled
+            specimen) on one host core.
+--impl reference times the oracle alone as the reference arm.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling);
+the path is not decomposed across GPUs.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and achieved HBM GB/s vs peak (FP32/BF16 vs FP64), adjoint/forward step cost"
+UNIT = "MLUPS"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-forms", action="store_true", help="skip the FP64 and 8192^2 side measurements")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "ours":
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist.init_process_group("gloo")
+    return rank, ws, dist
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_ctx(lbm, w, storage, U0, u0):
+    L = lbm.Lattice(w.nx, w.ny, dx=w.dx, c=w.c, omega=w.omega, storage=storage)
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [w.lam, w.mu])
+    lbm.lbm_set_body_force(L.ctx, *w.body_force)
+    kinds = {"periodic": lbm.LBM_BC_PERIODIC, "velocity": lbm.LBM_BC_VELOCITY, "traction": lbm.LBM_BC_TRACTION}
+    tfs = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "sin_pulse": 3, "ricker": 4}
+    for e, ed in enumerate(w.edges):
+        lbm.lbm_set_boundary(L.ctx, e, kinds[ed.kind], ed.value, tfs[ed.timefn], ed.tparams, ed.profile)
+    if U0 is not None:
+        lbm.lbm_init(L.ctx, U0, u0, 2)
+    return L
+
+
+def timed_steps(lbm, torch, L, steps, warmup, dist):
+    st = torch.cuda.current_stream()
+    lbm.lbm_step(L.ctx, warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lbm.lbm_profile(L.ctx, True)
+    e0.record(st)
+    lbm.lbm_step_async(L.ctx, steps)
+    e1.record(st)
+    e1.synchronize()
+    lbm.lbm_sync(L.ctx)
+    prof = lbm.lbm_profile_read(L.ctx)
+    lbm.lbm_profile(L.ctx, False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1), prof
+
+
+def recorded_traffic():
+    """DRAM bytes per bulk-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    try:
+        kv = dict(ln.split("=", 1) for ln in open(path).read().split() if "=" in ln)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in ("lbm_step.cu", "lbm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_26677_gb300", "csrc", f), "rb").read())
+    if kv.get("source_sha256") != h.hexdigest():
+        return None
+    try:
+        return float(kv["bytes_per_node"])
+    except Exception:
+        return None
+
+
+def run_ours(args, rank, ws, dist):
+    import numpy as np
+    import torch
+
+    from paper_2605_26677_gb300 import build
+
+    build.build()
+    from paper_2605_26677_gb300 import lbm
+    from synth import clamped_specimen, fourier_periodic
+
+    dev = torch.cuda.current_device()
+    w = clamped_specimen()
+    U0, u0 = w.fields()
+    N = w.nx * w.ny
+    L = setup_ctx(lbm, w, lbm.LBM_STORE_F32, U0, u0)
+    with ClockSampler(dev) as clk:
+        ms, prof = timed_steps(lbm, torch, L, args.steps, args.warmup, dist)
+    clocks = clk.summary()
+    bpn = lbm.lbm_bytes_per_node_update(L.ctx)
+    L.close()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = N * args.steps * ws / (ms_max * 1e-3) / 1e6
+
+    # roofline of the bulk kernel from its own event-timed launches
+    nl, tot = prof["step"]
+    kern_ms = tot / max(nl, 1)
+    achieved = bpn * N / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic_bpn = recorded_traffic()
+
+    # end to end through the C ABI with host buffers
+    U0p = torch.from_numpy(U0).pin_memory().numpy()
+    u0p = torch.from_numpy(u0).pin_memory().numpy()
+    uout = torch.empty((2, w.ny, w.nx), dtype=torch.float64).pin_memory().numpy()
+    Uout = torch.empty((6, w.ny, w.nx), dtype=torch.float64).pin_memory().numpy()
+    L = setup_ctx(lbm, w, lbm.LBM_STORE_F32, None, None)
+    lbm.lbm_init(L.ctx, U0p, u0p, 2)
+    lbm.lbm_step(L.ctx, args.warmup)
+    torch.cuda.synchronize()
+    chunk = 1000
+    n_out = 0
+    t0 = time.perf_counter()
+    lbm.lbm_init(L.ctx, U0p, u0p, 2)
+    done = 0
+    while done < args.steps:
+        k = min(chunk, args.steps - done)
+        lbm.lbm_step(L.ctx, k)
+        done += k
+        lbm.lbm_read_displacement(L.ctx, uout)
+        n_out += 1
+    lbm.lbm_read_state(L.ctx, Uout, None, want_P=False)
+    e2e_s = time.perf_counter() - t0
+    L.close()
+    h2d = (U0p.nbytes + u0p.nbytes) / args.steps
+    d2h = (n_out * uout.nbytes + Uout.nbytes) / args.steps
+    e2e = N * args.steps / e2e_s / 1e6
+
+    forms = {}
+    if not args.no_forms:
+        k = max(50, min(args.steps // 10, 400))
+        L = setup_ctx(lbm, w, lbm.LBM_STORE_F64, U0, u0)
+        ms64, prof64 = timed_steps(lbm, torch, L, k, 5, None)
+        b64 = lbm.lbm_bytes_per_node_update(L.ctx)
+        L.close()
+        n64, t64 = prof64["step"]
+        forms["fp64_clamped_specimen_4096x2048"] = {
+            "value": N * k / (ms64 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
+            "kernel_GBs": b64 * N / (t64 / max(n64, 1) * 1e-3) / 1e9, "bytes_per_node": b64,
+            "note": "FP64 populations (parity mode); FP64 ALU-bound on GB300"}
+        wp = fourier_periodic()
+        Up, up = wp.fields()
+        L = setup_ctx(lbm, wp, lbm.LBM_STORE_F32, Up, up)
+        del Up, up
+        ms8, prof8 = timed_steps(lbm, torch, L, k, 5, None)
+        L.close()
+        n8, t8 = prof8["step"]
+        N8 = wp.nx * wp.ny
+        forms["fp32_periodic_8192x8192"] = {
+            "value": N8 * k / (ms8 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
+            "kernel_GBs": bpn * N8 / (t8 / max(n8, 1) * 1e-3) / 1e9,
+            "roofline_frac": bpn * N8 / (t8 / max(n8, 1) * 1e-3) / 1e9 / peak,
+            "note": "16-mode random velocity field, NH lambda=1.5 mu=0.75, omega=2"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(seconds=12.0)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "clamped specimen 4096x2048 (NH lambda=2 mu=1, traction ramp 0.3 mu, body force "
+                               "1e-6, c=5, omega=1.95), FP32 populations + FP64 displacement",
+                   "nx": w.nx, "ny": w.ny, "global_batch": N * ws, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (%.2f GB moved per step)" % (bpn * N / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "traffic": None if traffic_bpn is None else traffic_bpn * N,
+                     "kernel": "k_step (fused pull-stream + collide + quadrature)",
+                     "bytes_per_node_update": bpn, "launch_ms": kern_ms,
+                     "edge_kernel_ms": prof["edges"][1] / max(prof["edges"][0], 1)},
+        "e2e": {"value": round(e2e, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof["step"][0] + prof["edges"][0]),
+        "clocks": clocks,
+        "forms": forms,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line
+
+
+def oracle_sample(nx=512, ny=256):
+    """The clamped specimen scaled to nx x ny, run by the FP64 oracle."""
+    from oracle import oracle as orc
+    from synth import clamped_specimen
+
+    w = clamped_specimen(nx=nx, ny=ny)
+    U0, u0 = w.fields()
+    O = orc.Lattice(w.nx, w.ny, w.dx, w.c, w.omega)
+    O.set_law(orc.NH, [w.lam, w.mu])
+    O.set_body_force(*w.body_force)
+    kinds = {"periodic": orc.PERIODIC, "velocity": orc.VELOCITY, "traction": orc.TRACTION}
+    tfs = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "sin_pulse": 3, "ricker": 4}
+    for e, ed in enumerate(w.edges):
+        O.set_edge(e, kinds[ed.kind], ed.value, tfs[ed.timefn], ed.tparams, ed.profile)
+    O.init(U0, u0, 2)
+    return O, w.nx * w.ny
+
+
+def cpu_baseline(seconds=12.0):
+    O, n = oracle_sample()
+    O.step(2)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        O.step(5)
+        steps += 5
+    dt = time.perf_counter() - t0
+    return {"value": round(n * steps / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "clamped specimen scaled to 512x256, %d steps (%.1f s) on one host core" % (steps, dt)}
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
+    if rank != 0:
+        return None
+    O, n = oracle_sample(nx=256, ny=128)
+    O.step(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    O.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "clamped specimen (FP64 CPU oracle), each step a 256x128 scaled sample",
+                       "nx": 256, "ny": 128},
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "clamped specimen scaled to 256x128, %d steps" % args.steps},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, ws, dist = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, rank, ws)
+    else:
+        line = run_ours(args, rank, ws, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the total-Lagrangian
+ * vectorial lattice Boltzmann method for finite-strain hyperelastic dynamics
+ * (Feng & Chu): a D2Q4 lattice whose four populations per node are
+ * six-component vectors carrying the material velocity v and the deformation
+ * gradient F.
+ *
+ * Model (paper sections and equations):
+ *   state     U = (v1, v2, F11, F12, F21, F22)                 Sec. 2.4, Eq. (5)
+ *   system    dU/dt + dPhi_X/dX + dPhi_Y/dY = B                 Eqs. (6)-(7)
+ *   lattice   q = (1,0), (0,1), (-1,0), (0,-1), c = dx/dt        Sec. 3.1
+ *   one step  recover U, P(F), equilibrium, BGK collision with
+ *             trapezoidal source, streaming, half-way edges,
+ *             displacement quadrature                          Sec. 3.7
+ *
+ * Conventions shared by every call:
+ *   - Every function returns lbm_status; nothing is thrown and nothing aborts.
+ *     On an error the context is left as it was before the call unless the
+ *     description says otherwise, and lbm_last_error() explains it.
+ *   - Node (ix, iy), 0 <= ix < nx, 0 <= iy < ny, sits at material point
+ *     X = ((ix + 1/2) dx, (iy + 1/2) dx); half-way walls lie dx/2 outside the
+ *     first and last node of a non-periodic direction (Sec. 3.6).
+ *   - Field arrays are float64, component-major, x fastest:
+ *     a[(m * ny + iy) * nx + ix] for component m. N = nx * ny.
+ *     U fields have 6 components in the order above, displacement 2 (u1, u2),
+ *     stress 4 (P11, P12, P21, P22) or (s11, s12, s21, s22).
+ *   - "host" pointers are ordinary (preferably pinned) host memory owned by
+ *     the caller and only read or written during the call. "device" pointers
+ *     are device memory of the context's GPU owned by the caller; the call
+ *     enqueues work that uses them on the context's stream and returns
+ *     without waiting.
+ *   - All device work of a context runs on lbm_config.stream (NULL = the
+ *     legacy default stream). A context must not be used from two host
+ *     threads at once.
+ *   - Device-side conditions (J <= 0, a traction Newton solve that did not
+ *     converge, a non-finite state) are latched in a device status word; the
+ *     next call that synchronises (lbm_step, lbm_sync, lbm_read_*) returns the
+ *     matching LBM_ERR_* code. The state stays readable after such an error.
+ *     lbm_init clears the latch.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_API_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,            /* an argument is out of range or inconsistent        */
+    LBM_ERR_STATE = 2,          /* call out of order (e.g. step before init)          */
+    LBM_ERR_OOM = 3,            /* device or host allocation failed                   */
+    LBM_ERR_CUDA = 4,           /* a CUDA runtime call failed                         */
+    LBM_ERR_NONPOSITIVE_J = 5,  /* some node reached J = det F <= 0 (Sec. 2.2)        */
+    LBM_ERR_NEWTON = 6,         /* a traction-edge Newton solve failed (Sec. 3.6.2)   */
+    LBM_ERR_NONFINITE = 7,      /* the state became NaN or infinite                   */
+    LBM_ERR_UNSUPPORTED = 8     /* valid request this build does not implement        */
+} lbm_status;
+
+/* Storage of the populations. Compute is in the storage precision (F64, F32).
+ * Populations are stored as offsets from the rest-state equilibrium
+ * f_rest = (0, 0, 1/4, 0, 0, 1/4) (Eq. 12 at U = (0,0,1,0,0,1), P(I) = 0). */
+typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16 = 3 } lbm_storage;
+
+/* Edges and their outward normals N: left (-1,0), right (1,0), bottom (0,-1), top (0,1). */
+typedef enum { LBM_EDGE_LEFT = 0, LBM_EDGE_RIGHT = 1, LBM_EDGE_BOTTOM = 2, LBM_EDGE_TOP = 3 } lbm_edge;
+
+/* Edge rules: wrap-around, velocity Dirichlet (Eq. 24), nominal-traction
+ * Neumann (Eq. 25). Periodic must be set on both opposite edges. */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_VELOCITY = 1, LBM_BC_TRACTION = 2 } lbm_bc;
+
+/* Hyperelastic closures of Appendix A. Parameters:
+ *   SVK, NH, LOGNH: {lambda, mu}        (Eqs. A.4, A.5, A.6)
+ *   MR: {lambda, c10, c01}; YEOH: {lambda, c1, c2, c3}; GENT: {lambda, mu, Jm} */
+typedef enum { LBM_LAW_SVK = 0, LBM_LAW_NH = 1, LBM_LAW_LOGNH = 2, LBM_LAW_MR = 3,
+               LBM_LAW_YEOH = 4, LBM_LAW_GENT = 5 } lbm_law;
+
+/* Edge-data time functions g(t); the edge value is value * profile[s] * g(t),
+ * evaluated at t^n + dt/2 (Eq. 23). tparams:
+ *   CONST: -;  LINEAR_RAMP: {T}: min(t/T, 1);
+ *   SIN2_RAMP: {T}: sin^2(pi t / (2T)) for t < T, else 1      (shape of Eq. 33)
+ *   SIN_PULSE: {T}: sin(pi t / T) for t < T, else 0            (shape of Eq. 35)
+ *   RICKER: {s, t0, t_end}: 2/(sqrt(3s) pi^(1/4)) (1 - z^2) exp(-z^2/2),
+ *           z = (t - t0)/s, for t <= t_end, else 0              (Sec. 5.4) */
+typedef enum { LBM_T_CONST = 0, LBM_T_LINEAR_RAMP = 1, LBM_T_SIN2_RAMP = 2, LBM_T_SIN_PULSE = 3,
+               LBM_T_RICKER = 4 } lbm_timefn;
+
+/* Tangential column of the traction-edge boundary deformation gradient F^b
+ * (Sec. 3.6.2; the normal column always solves P(F^b) N = T by Newton):
+ *   NODE:    F at the boundary node at t^n -- the form that reproduces the
+ *            paper's mixed-boundary results (Table 2);
+ *   EXTRAP2: linear extrapolation to the wall plus the half-step kinematic
+ *            shift (dt/2) dv/dT, so F^b = F(X_b, t + dt/2) + O(dt^2) (Eq. B.20). */
+typedef enum { LBM_FB_NODE = 0, LBM_FB_EXTRAP2 = 1 } lbm_fb_mode;
+
+typedef struct {
+    int32_t nx, ny;    /* nodes; >= 1 (>= 3 along a non-periodic direction)       */
+    double dx;         /* lattice spacing, > 0                                    */
+    double c;          /* lattice speed c = dx/dt, > 0 (Sec. 3.1)                 */
+    double omega;      /* BGK relaxation rate, 0 < omega <= 2 (Eq. 14)            */
+    int32_t storage;   /* lbm_storage                                             */
+    int32_t fb_mode;   /* lbm_fb_mode                                             */
+    int32_t device;    /* CUDA device ordinal                                     */
+    void *stream;      /* cudaStream_t used for all device work; NULL = default    */
+} lbm_config;
+
+/* Create a context and allocate its device state (two population buffers of
+ * 24 planes each, the FP64 displacement accumulator u*, a status word). Sizes
+ * are checked: LBM_ERR_ARG for invalid or oversize grids, LBM_ERR_OOM when the
+ * device cannot hold the state. On success *out owns the allocation. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
+
+/* Free everything the context owns. NULL is accepted. Waits for the
+ * context's stream. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Text of the last error on ctx (or of the last failed lbm_create on this
+ * host thread when ctx is NULL). Valid until the next call on ctx. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A). Must be
+ * called before lbm_init. LBM_ERR_UNSUPPORTED for MR, YEOH, GENT. */
+lbm_status lbm_set_material(lbm_ctx *ctx, int32_t law, const double *params, int32_t nparams);
+
+/* Uniform body acceleration b = (b1, b2) of Eq. (1); B = (b1, b2, 0, 0, 0, 0)
+ * enters the state recovery (Eq. 10) and the collision source (Eq. 14).
+ * Must be called before lbm_init (default 0). */
+lbm_status lbm_set_body_force(lbm_ctx *ctx, double b1, double b2);
+
+/* Rule and data of one edge. value[2] is v_D for LBM_BC_VELOCITY and the
+ * nominal traction T (per reference length) for LBM_BC_TRACTION; both are
+ * ignored for LBM_BC_PERIODIC. tparams[4] per lbm_timefn (NULL = zeros).
+ * profile (host, NULL = 1) holds one factor per edge node (ny for left and
+ * right, nx for bottom and top) and is copied. May be called again between
+ * steps; the new data applies from the next step. Default: periodic. */
+lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t edge, int32_t bc, const double value[2],
+                            int32_t timefn, const double tparams[4], const double *profile);
+
+/* Initial state (Sec. 3.4 and 3.5). U0 (host, 6N) holds v0 and F0 = I + Grad u0;
+ * u0 (host, 2N, NULL = 0) the initial displacement. order 0 starts from the
+ * equilibrium f^eq(U0); order 2 uses f_q = f^eq(U0) - (dt/2) D_q f^eq(U0)
+ * (Eqs. 16-21) with second-order central differences (one-sided three-point
+ * stencils next to non-periodic edges) for the gradients. Sets t = 0, clears
+ * the status latch and starts u* = u0 - (dt/2) v0. Requires lbm_set_material;
+ * checks edge pairing and c > sqrt(lambda + 2 mu) (the rest-state P-wave
+ * speed). Synchronises. */
+lbm_status lbm_init(lbm_ctx *ctx, const double *U0, const double *u0, int32_t order);
+
+/* As lbm_init with device pointers (6N and 2N float64, NULL u0 = 0); enqueued
+ * on the stream, does not synchronise. */
+lbm_status lbm_init_device(lbm_ctx *ctx, const double *U0_dev, const double *u0_dev, int32_t order);
+
+/* Advance nsteps >= 0 time steps (Sec. 3.7), then wait and return the
+ * latched device status. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* As lbm_step without waiting; check later with lbm_sync. */
+lbm_status lbm_step_async(lbm_ctx *ctx, int64_t nsteps);
+
+/* Wait for the context's stream and return the latched device status. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Current time level n: U^n (6N), P(F^n) (4N, NULL to skip) into host arrays,
+ * and t^n = n dt into *t (NULL to skip). Synchronises. */
+lbm_status lbm_read_state(lbm_ctx *ctx, double *U, double *P, double *t);
+lbm_status lbm_read_state_device(lbm_ctx *ctx, double *U_dev, double *P_dev);
+
+/* Displacement u^n = u*^n + (dt/2) v^n (Eq. 22), 2N float64. */
+lbm_status lbm_read_displacement(lbm_ctx *ctx, double *u);
+lbm_status lbm_read_displacement_device(lbm_ctx *ctx, double *u_dev);
+
+/* Cauchy stress sigma = J^{-1} P F^T (Sec. 3.5), 4N float64 host. */
+lbm_status lbm_read_cauchy(lbm_ctx *ctx, double *sigma);
+
+/* Global diagnostics of the current state, reduced in FP64:
+ * out[0..1] sum over nodes of v1, v2; out[2..5] mean F11, F12, F21, F22;
+ * out[6] energy dx^2 sum (|v|^2 / 2 + W(F)); out[7] min J; out[8] max J;
+ * out[9] max over nodes of the Frobenius norm |F - I|. Synchronises. */
+lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[10]);
+
+/* Checkpoint: populations, u*, step count. With buf == NULL, *bytes receives
+ * the size needed. lbm_load restores a checkpoint of the same nx, ny and
+ * storage (LBM_ERR_ARG otherwise) into an initialised context. */
+lbm_status lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes);
+lbm_status lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Step count n, time t^n and time step dt (any may be NULL). No device work. */
+lbm_status lbm_info(lbm_ctx *ctx, int64_t *step, double *t, double *dt);
+
+/* Per-kernel timing with CUDA events on the context's stream. enable != 0
+ * starts recording (and clears earlier records), 0 stops. lbm_profile_read
+ * synchronises and returns, for each of the kernels below, the number of
+ * timed launches and their total device time in milliseconds:
+ *   out[0], out[1]: fused collide-stream kernel (launches, ms)
+ *   out[2], out[3]: edge reconstruction kernel  (launches, ms) */
+lbm_status lbm_profile(lbm_ctx *ctx, int32_t enable);
+lbm_status lbm_profile_read(lbm_ctx *ctx, double out[4]);
+
+/* Algorithmic bytes one node-update of the fused step moves in and out of
+ * HBM for this context's storage (populations read and written, u* read and
+ * written). */
+double lbm_bytes_per_node_update(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

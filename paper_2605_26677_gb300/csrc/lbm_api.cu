@@ -1,0 +1,699 @@
+// lbm_api.cu -- implementation of the C ABI declared in include/lbm.h.
+//
+// The context owns two population buffers (each 24 planes, layout in
+// lbm_device.cuh), the FP64 displacement accumulator u*, a device status word,
+// a device step counter and a small diagnostics scratch area. Every device
+// operation is enqueued on the stream given at creation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace tlv;
+
+struct lbm_ctx {
+    lbm_config cfg{};
+    cudaStream_t st = nullptr;
+    int eb = 4;            // bytes per stored population value
+    Layout L{};
+    void *f[2] = {nullptr, nullptr};
+    double *ustar = nullptr;
+    int *d_status = nullptr;
+    long long *d_step = nullptr;
+    double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
+    double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
+    int cur = 0;
+    long long step = 0;
+    double dt = 0.0;
+    Material m{};
+    bool have_material = false;
+    double b[2] = {0.0, 0.0};
+    EdgeDesc edge[4]{};
+    bool initialized = false;
+    int grid_step = 1;
+    int edge_blk_end[4] = {0, 0, 0, 0};
+    std::string err;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_step, ev_edge; // start/stop pairs
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError(); // clear a non-sticky error
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, msg);
+}
+
+#define CK(ctx, call)                                                       \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);          \
+    } while (0)
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+int edge_len(const lbm_ctx *c, int e) { return (e <= EDGE_RIGHT) ? c->L.ny : c->L.nx; }
+
+bool xper(const lbm_ctx *c) { return c->edge[EDGE_LEFT].kind == BC_PERIODIC; }
+bool yper(const lbm_ctx *c) { return c->edge[EDGE_BOTTOM].kind == BC_PERIODIC; }
+
+// Edge pairing and minimum sizes (one-sided three-point stencils need 3 nodes).
+lbm_status check_edges(lbm_ctx *c)
+{
+    if ((c->edge[EDGE_LEFT].kind == BC_PERIODIC) != (c->edge[EDGE_RIGHT].kind == BC_PERIODIC))
+        return fail(c, LBM_ERR_ARG, "left and right edges must both be periodic or both non-periodic");
+    if ((c->edge[EDGE_BOTTOM].kind == BC_PERIODIC) != (c->edge[EDGE_TOP].kind == BC_PERIODIC))
+        return fail(c, LBM_ERR_ARG, "bottom and top edges must both be periodic or both non-periodic");
+    if (!xper(c) && c->L.nx < 3) return fail(c, LBM_ERR_ARG, "nx >= 3 is needed with non-periodic left/right edges");
+    if (!yper(c) && c->L.ny < 3) return fail(c, LBM_ERR_ARG, "ny >= 3 is needed with non-periodic bottom/top edges");
+    return LBM_OK;
+}
+
+lbm_status map_flags(lbm_ctx *c, int flags)
+{
+    if (flags & ST_NONFINITE) return fail(c, LBM_ERR_NONFINITE, "the state became non-finite");
+    if (flags & ST_BAD_J) return fail(c, LBM_ERR_NONPOSITIVE_J, "a node reached J = det F <= 0");
+    if (flags & ST_NEWTON) return fail(c, LBM_ERR_NEWTON, "a traction-edge Newton solve did not converge");
+    return LBM_OK;
+}
+
+lbm_status sync_status(lbm_ctx *c)
+{
+    int flags = 0;
+    CK(c, cudaMemcpyAsync(&flags, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return map_flags(c, flags);
+}
+
+template <typename T>
+StepArgs<T> step_args(const lbm_ctx *c, int cur)
+{
+    StepArgs<T> a;
+    a.fin = static_cast<const T *>(c->f[cur]);
+    a.fout = static_cast<T *>(c->f[cur ^ 1]);
+    a.ustar = c->ustar;
+    a.status = c->d_status;
+    a.step = c->d_step;
+    a.L = c->L;
+    const double w = c->cfg.omega;
+    a.omega = (T)w;
+    a.one_m_omega = (T)(1.0 - w);
+    a.inv2c = (T)(0.5 / c->cfg.c);
+    a.quarter = (T)0.25;
+    a.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
+    a.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
+    a.src1 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[0]);
+    a.src2 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[1]);
+    a.lam = (T)c->m.lam;
+    a.mu = (T)c->m.mu;
+    a.dt = c->dt;
+    return a;
+}
+
+EdgeArgs edge_args(const lbm_ctx *c, int cur)
+{
+    EdgeArgs a;
+    a.f = c->f[cur];
+    a.L = c->L;
+    for (int e = 0; e < 4; ++e) {
+        a.e[e] = c->edge[e];
+        a.blk_end[e] = c->edge_blk_end[e];
+    }
+    a.m = c->m;
+    a.c = c->cfg.c;
+    a.dt = c->dt;
+    a.dx = c->cfg.dx;
+    a.hdtb1 = 0.5 * c->dt * c->b[0];
+    a.hdtb2 = 0.5 * c->dt * c->b[1];
+    a.fb_mode = c->cfg.fb_mode;
+    a.xper = xper(c);
+    a.yper = yper(c);
+    a.step = c->d_step;
+    a.status = c->d_status;
+    return a;
+}
+
+void clear_profile(lbm_ctx *c)
+{
+    for (cudaEvent_t e : c->ev_step) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_edge) cudaEventDestroy(e);
+    c->ev_step.clear();
+    c->ev_edge.clear();
+}
+
+lbm_status record(lbm_ctx *c, std::vector<cudaEvent_t> &v)
+{
+    cudaEvent_t e;
+    CK(c, cudaEventCreate(&e));
+    v.push_back(e);
+    CK(c, cudaEventRecord(e, c->st));
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status do_step(lbm_ctx *c, int64_t nsteps)
+{
+    const bool prof = c->prof && (c->ev_step.size() < 200000);
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const EdgeArgs ea = edge_args(c, c->cur);
+        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+        CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
+        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+        const StepArgs<T> sa = step_args<T>(c, c->cur);
+        if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
+        CK(c, launch_step(c->eb, c->m.law, &sa, c->grid_step, c->st));
+        if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status read_device(lbm_ctx *c, double *U, double *P, double *sigma, double *u)
+{
+    ReadArgs a;
+    a.f = c->f[c->cur];
+    a.ustar = c->ustar;
+    a.L = c->L;
+    a.m = c->m;
+    a.dt = c->dt;
+    a.b1 = c->b[0];
+    a.b2 = c->b[1];
+    a.U = U;
+    a.P = P;
+    a.sigma = sigma;
+    a.u = u;
+    CK(c, launch_read(c->eb, a, c->st));
+    return LBM_OK;
+}
+
+// run fn(device buffer) then copy `count` doubles to host `dst`
+template <typename Fn>
+lbm_status read_to_host(lbm_ctx *c, double *dst, size_t count, Fn fn)
+{
+    double *tmp = nullptr;
+    CK(c, cudaMallocAsync((void **)&tmp, count * sizeof(double), c->st));
+    lbm_status s = fn(tmp);
+    if (s == LBM_OK) {
+        cudaError_t e = cudaMemcpyAsync(dst, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "cudaMemcpyAsync");
+    }
+    cudaFreeAsync(tmp, c->st);
+    if (s != LBM_OK) return s;
+    return sync_status(c);
+}
+
+lbm_status check_ready(lbm_ctx *c)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_init has not been called");
+    CK(c, cudaSetDevice(c->cfg.device));
+    return LBM_OK;
+}
+
+struct SaveHeader {
+    char magic[8];
+    int32_t version, nx, ny, eb;
+    int64_t step;
+};
+
+} // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, LBM_ERR_ARG, "cfg is NULL");
+    if (cfg->nx < 1 || cfg->ny < 1) return fail(nullptr, LBM_ERR_ARG, "nx and ny must be >= 1 (empty lattice)");
+    if (cfg->nx > (1 << 24) || cfg->ny > (1 << 24)) return fail(nullptr, LBM_ERR_ARG, "nx or ny above 2^24");
+    if (!(cfg->dx > 0.0) || !is_finite(cfg->dx)) return fail(nullptr, LBM_ERR_ARG, "dx must be finite and > 0");
+    if (!(cfg->c > 0.0) || !is_finite(cfg->c)) return fail(nullptr, LBM_ERR_ARG, "c must be finite and > 0");
+    if (!(cfg->omega > 0.0) || !(cfg->omega <= 2.0)) return fail(nullptr, LBM_ERR_ARG, "omega must be in (0, 2]");
+    if (cfg->storage == LBM_STORE_BF16 || cfg->storage == LBM_STORE_F16)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "BF16/FP16 offset storage is not built in this version");
+    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32)
+        return fail(nullptr, LBM_ERR_ARG, "unknown storage");
+    if (cfg->fb_mode != LBM_FB_NODE && cfg->fb_mode != LBM_FB_EXTRAP2) return fail(nullptr, LBM_ERR_ARG, "unknown fb_mode");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->st = static_cast<cudaStream_t>(cfg->stream);
+    c->eb = (cfg->storage == LBM_STORE_F64) ? 8 : 4;
+    c->dt = cfg->dx / cfg->c;
+    const int line = 128 / c->eb, vec = 16 / c->eb;
+    c->L.nx = cfg->nx;
+    c->L.ny = cfg->ny;
+    c->L.xoff = line;
+    c->L.pitch = (int)round_up((long long)line + cfg->nx + vec, line);
+    c->L.plane = (long long)(cfg->ny + 2) * c->L.pitch;
+    c->L.upitch = (int)round_up((long long)cfg->nx + 4, 16);
+    c->L.uplane = (long long)cfg->ny * c->L.upitch;
+    for (int e = 0; e < 4; ++e) {
+        c->edge[e] = EdgeDesc{};
+        c->edge[e].kind = BC_PERIODIC;
+    }
+    int blk = 0;
+    for (int e = 0; e < 4; ++e) {
+        blk += (edge_len(c, e) + 127) / 128;
+        c->edge_blk_end[e] = blk;
+    }
+    const size_t fbytes = (size_t)24 * (size_t)c->L.plane * c->eb;
+    const size_t ubytes = (size_t)2 * (size_t)c->L.uplane * sizeof(double);
+
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) {
+        lbm_status s = cuda_fail(nullptr, e, "cudaSetDevice");
+        delete c;
+        return s;
+    }
+#define CKC(call)                                                   \
+    do {                                                            \
+        cudaError_t e2 = (call);                                    \
+        if (e2 != cudaSuccess) {                                    \
+            lbm_status s2 = cuda_fail(nullptr, e2, #call);          \
+            lbm_destroy(c);                                         \
+            return s2;                                              \
+        }                                                           \
+    } while (0)
+    CKC(cudaMalloc(&c->f[0], fbytes));
+    CKC(cudaMalloc(&c->f[1], fbytes));
+    CKC(cudaMalloc((void **)&c->ustar, ubytes));
+    CKC(cudaMalloc((void **)&c->d_status, sizeof(int)));
+    CKC(cudaMalloc((void **)&c->d_step, sizeof(long long)));
+    CKC(cudaMalloc((void **)&c->d_diag, (size_t)(diag_blocks(c->L) * 10 + 10) * sizeof(double)));
+    CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->st));
+    CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->st));
+    CKC(cudaMemsetAsync(c->ustar, 0, ubytes, c->st));
+    CKC(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    CKC(cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->st));
+    CKC(cudaStreamSynchronize(c->st));
+#undef CKC
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    c->grid_step = sms > 0 ? sms : 1; // refined in lbm_set_material (depends on the law)
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->cfg.device);
+    cudaStreamSynchronize(c->st);
+    clear_profile(c);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->ustar);
+    cudaFree(c->d_status);
+    cudaFree(c->d_step);
+    cudaFree(c->d_diag);
+    for (int e = 0; e < 4; ++e) cudaFree(c->d_profile[e]);
+    delete c;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32_t nparams)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (c->initialized) return fail(c, LBM_ERR_STATE, "the material must be set before lbm_init");
+    if (law == LBM_LAW_MR || law == LBM_LAW_YEOH || law == LBM_LAW_GENT)
+        return fail(c, LBM_ERR_UNSUPPORTED, "Mooney-Rivlin, Yeoh and Gent closures are not built in this version");
+    if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH) return fail(c, LBM_ERR_ARG, "unknown law");
+    if (!params || nparams < 2) return fail(c, LBM_ERR_ARG, "expected params {lambda, mu}");
+    if (!is_finite(params[0]) || !is_finite(params[1]) || !(params[1] > 0.0))
+        return fail(c, LBM_ERR_ARG, "lambda must be finite and mu finite and > 0");
+    if (!(params[0] + 2.0 * params[1] > 0.0)) return fail(c, LBM_ERR_ARG, "lambda + 2 mu must be > 0");
+    c->m.law = law; // LBM_LAW_* and tlv::LAW_* share values for SVK, NH, LOGNH
+    c->m.lam = params[0];
+    c->m.mu = params[1];
+    c->have_material = true;
+    CK(c, cudaSetDevice(c->cfg.device));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    const int per_sm = step_blocks_per_sm(c->eb, c->m.law);
+    const int vec = step_vec(c->eb);
+    const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
+    const long long needed = (tasks + 3) / 4; // 4 warps per block
+    long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (g > needed) g = needed;
+    c->grid_step = (int)(g < 1 ? 1 : g);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_body_force(lbm_ctx *c, double b1, double b2)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (c->initialized) return fail(c, LBM_ERR_STATE, "the body force must be set before lbm_init");
+    if (!is_finite(b1) || !is_finite(b2)) return fail(c, LBM_ERR_ARG, "body force must be finite");
+    c->b[0] = b1;
+    c->b[1] = b2;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_boundary(lbm_ctx *c, int32_t edge, int32_t bc, const double value[2], int32_t timefn,
+                            const double tparams[4], const double *profile)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (edge < 0 || edge > 3) return fail(c, LBM_ERR_ARG, "edge must be 0..3");
+    if (bc < LBM_BC_PERIODIC || bc > LBM_BC_TRACTION) return fail(c, LBM_ERR_ARG, "unknown boundary kind");
+    if (timefn < LBM_T_CONST || timefn > LBM_T_RICKER) return fail(c, LBM_ERR_ARG, "unknown time function");
+    EdgeDesc d{};
+    d.kind = bc;
+    d.timefn = timefn;
+    d.value[0] = value ? value[0] : 0.0;
+    d.value[1] = value ? value[1] : 0.0;
+    for (int i = 0; i < 4; ++i) d.tp[i] = tparams ? tparams[i] : 0.0;
+    if (!is_finite(d.value[0]) || !is_finite(d.value[1])) return fail(c, LBM_ERR_ARG, "edge value must be finite");
+    for (int i = 0; i < 4; ++i)
+        if (!is_finite(d.tp[i])) return fail(c, LBM_ERR_ARG, "time-function parameters must be finite");
+    if ((timefn == LBM_T_LINEAR_RAMP || timefn == LBM_T_SIN2_RAMP || timefn == LBM_T_SIN_PULSE) && !(d.tp[0] > 0.0))
+        return fail(c, LBM_ERR_ARG, "ramp and pulse durations must be > 0");
+    if (timefn == LBM_T_RICKER && !(d.tp[0] > 0.0)) return fail(c, LBM_ERR_ARG, "Ricker width must be > 0");
+    const int len = edge_len(c, edge);
+    if (profile)
+        for (int i = 0; i < len; ++i)
+            if (!is_finite(profile[i])) return fail(c, LBM_ERR_ARG, "profile must be finite");
+    CK(c, cudaSetDevice(c->cfg.device));
+    // an earlier edge kernel may still read the old profile
+    CK(c, cudaStreamSynchronize(c->st));
+    if (profile) {
+        if (!c->d_profile[edge]) CK(c, cudaMalloc((void **)&c->d_profile[edge], (size_t)len * sizeof(double)));
+        CK(c, cudaMemcpy(c->d_profile[edge], profile, (size_t)len * sizeof(double), cudaMemcpyHostToDevice));
+        d.profile = c->d_profile[edge];
+    } else {
+        d.profile = nullptr;
+    }
+    c->edge[edge] = d;
+    return LBM_OK;
+}
+
+static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
+{
+    InitArgs a;
+    a.U0 = U0_dev;
+    a.u0 = u0_dev;
+    a.fout = c->f[0];
+    a.ustar = c->ustar;
+    a.status = c->d_status;
+    a.L = c->L;
+    a.m = c->m;
+    a.c = c->cfg.c;
+    a.dt = c->dt;
+    a.dx = c->cfg.dx;
+    a.omega = c->cfg.omega;
+    a.b1 = c->b[0];
+    a.b2 = c->b[1];
+    a.order = order;
+    a.xper = xper(c);
+    a.yper = yper(c);
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    CK(c, cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->st));
+    CK(c, launch_init(c->eb, a, c->st));
+    c->cur = 0;
+    c->step = 0;
+    c->initialized = true;
+    return LBM_OK;
+}
+
+static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!c->have_material) return fail(c, LBM_ERR_STATE, "lbm_set_material must precede lbm_init");
+    if (!U0) return fail(c, LBM_ERR_ARG, "U0 is NULL");
+    if (order != 0 && order != 2) return fail(c, LBM_ERR_ARG, "order must be 0 or 2");
+    lbm_status s = check_edges(c);
+    if (s != LBM_OK) return s;
+    const double cP = std::sqrt(c->m.lam + 2.0 * c->m.mu);
+    if (!(c->cfg.c > cP)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "lattice speed c = %g must exceed the P-wave speed sqrt(lambda + 2 mu) = %g",
+                      c->cfg.c, cP);
+        return fail(c, LBM_ERR_ARG, buf);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t order)
+{
+    lbm_status s = init_checks(c, U0, order);
+    if (s != LBM_OK) return s;
+    CK(c, cudaSetDevice(c->cfg.device));
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    double *dU = nullptr, *du = nullptr;
+    CK(c, cudaMallocAsync((void **)&dU, 6 * N * sizeof(double), c->st));
+    cudaError_t e = cudaMemcpyAsync(dU, U0, 6 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && u0) {
+        e = cudaMallocAsync((void **)&du, 2 * N * sizeof(double), c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(du, u0, 2 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    }
+    if (e == cudaSuccess) s = init_common(c, dU, du, order);
+    cudaFreeAsync(dU, c->st);
+    if (du) cudaFreeAsync(du, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copying the initial state");
+    if (s != LBM_OK) return s;
+    return sync_status(c);
+}
+
+lbm_status lbm_init_device(lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
+{
+    lbm_status s = init_checks(c, U0_dev, order);
+    if (s != LBM_OK) return s;
+    CK(c, cudaSetDevice(c->cfg.device));
+    return init_common(c, U0_dev, u0_dev, order);
+}
+
+lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
+    s = check_edges(c);
+    if (s != LBM_OK) return s;
+    return (c->eb == 8) ? do_step<double>(c, nsteps) : do_step<float>(c, nsteps);
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
+{
+    lbm_status s = lbm_step_async(c, nsteps);
+    if (s != LBM_OK) return s;
+    return sync_status(c);
+}
+
+lbm_status lbm_sync(lbm_ctx *c)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    return sync_status(c);
+}
+
+lbm_status lbm_read_state(lbm_ctx *c, double *U, double *P, double *t)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!U) return fail(c, LBM_ERR_ARG, "U is NULL");
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    if (t) *t = c->step * c->dt;
+    s = read_to_host(c, U, 6 * N, [&](double *d) { return read_device(c, d, nullptr, nullptr, nullptr); });
+    if (s != LBM_OK && s != LBM_ERR_NONFINITE && s != LBM_ERR_NONPOSITIVE_J && s != LBM_ERR_NEWTON) return s;
+    if (!P) return s;
+    lbm_status s2 = read_to_host(c, P, 4 * N, [&](double *d) { return read_device(c, nullptr, d, nullptr, nullptr); });
+    return s != LBM_OK ? s : s2;
+}
+
+lbm_status lbm_read_state_device(lbm_ctx *c, double *U_dev, double *P_dev)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!U_dev && !P_dev) return fail(c, LBM_ERR_ARG, "both outputs are NULL");
+    return read_device(c, U_dev, P_dev, nullptr, nullptr);
+}
+
+lbm_status lbm_read_displacement(lbm_ctx *c, double *u)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!u) return fail(c, LBM_ERR_ARG, "u is NULL");
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    return read_to_host(c, u, 2 * N, [&](double *d) { return read_device(c, nullptr, nullptr, nullptr, d); });
+}
+
+lbm_status lbm_read_displacement_device(lbm_ctx *c, double *u_dev)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!u_dev) return fail(c, LBM_ERR_ARG, "u is NULL");
+    return read_device(c, nullptr, nullptr, nullptr, u_dev);
+}
+
+lbm_status lbm_read_cauchy(lbm_ctx *c, double *sigma)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!sigma) return fail(c, LBM_ERR_ARG, "sigma is NULL");
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    return read_to_host(c, sigma, 4 * N, [&](double *d) { return read_device(c, nullptr, nullptr, d, nullptr); });
+}
+
+lbm_status lbm_diagnostics(lbm_ctx *c, double out[10])
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    DiagArgs a;
+    a.f = c->f[c->cur];
+    a.L = c->L;
+    a.m = c->m;
+    a.dt = c->dt;
+    a.dx = c->cfg.dx;
+    a.b1 = c->b[0];
+    a.b2 = c->b[1];
+    a.partial = c->d_diag;
+    a.out = c->d_diag + (size_t)diag_blocks(c->L) * 10;
+    CK(c, launch_diag(c->eb, a, c->st));
+    CK(c, cudaMemcpyAsync(out, a.out, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    return sync_status(c);
+}
+
+lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!bytes) return fail(c, LBM_ERR_ARG, "bytes is NULL");
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    const size_t need = sizeof(SaveHeader) + 24 * N * c->eb + 2 * N * sizeof(double);
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (*bytes < need) return fail(c, LBM_ERR_ARG, "buffer too small");
+    SaveHeader h{};
+    std::memcpy(h.magic, "TLVLBM01", 8);
+    h.version = 1;
+    h.nx = c->L.nx;
+    h.ny = c->L.ny;
+    h.eb = c->eb;
+    h.step = c->step;
+    std::memcpy(buf, &h, sizeof h);
+    char *p = static_cast<char *>(buf) + sizeof h;
+    const size_t rowb = (size_t)c->L.nx * c->eb;
+    for (int pl = 0; pl < 24; ++pl) {
+        const char *src = static_cast<const char *>(c->f[c->cur]) +
+                          ((size_t)pl * c->L.plane + c->L.pitch + c->L.xoff) * c->eb;
+        CK(c, cudaMemcpy2DAsync(p, rowb, src, (size_t)c->L.pitch * c->eb, rowb, c->L.ny, cudaMemcpyDeviceToHost, c->st));
+        p += rowb * c->L.ny;
+    }
+    for (int k = 0; k < 2; ++k) {
+        CK(c, cudaMemcpy2DAsync(p, (size_t)c->L.nx * sizeof(double), c->ustar + k * c->L.uplane,
+                                (size_t)c->L.upitch * sizeof(double), (size_t)c->L.nx * sizeof(double), c->L.ny,
+                                cudaMemcpyDeviceToHost, c->st));
+        p += N * sizeof(double);
+    }
+    *bytes = need;
+    return sync_status(c);
+}
+
+lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
+{
+    lbm_status s = check_ready(c);
+    if (s != LBM_OK) return s;
+    if (!buf || bytes < sizeof(SaveHeader)) return fail(c, LBM_ERR_ARG, "buffer too small");
+    SaveHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    if (std::memcmp(h.magic, "TLVLBM01", 8) != 0 || h.version != 1) return fail(c, LBM_ERR_ARG, "not a checkpoint");
+    if (h.nx != c->L.nx || h.ny != c->L.ny || h.eb != c->eb)
+        return fail(c, LBM_ERR_ARG, "checkpoint grid or storage differs from the context");
+    if (bytes < sizeof h + 24 * N * c->eb + 2 * N * sizeof(double)) return fail(c, LBM_ERR_ARG, "truncated checkpoint");
+    CK(c, cudaStreamSynchronize(c->st));
+    const char *p = static_cast<const char *>(buf) + sizeof h;
+    const size_t rowb = (size_t)c->L.nx * c->eb;
+    c->cur = 0;
+    for (int pl = 0; pl < 24; ++pl) {
+        char *dst = static_cast<char *>(c->f[0]) + ((size_t)pl * c->L.plane + c->L.pitch + c->L.xoff) * c->eb;
+        CK(c, cudaMemcpy2DAsync(dst, (size_t)c->L.pitch * c->eb, p, rowb, rowb, c->L.ny, cudaMemcpyHostToDevice, c->st));
+        p += rowb * c->L.ny;
+    }
+    for (int k = 0; k < 2; ++k) {
+        CK(c, cudaMemcpy2DAsync(c->ustar + k * c->L.uplane, (size_t)c->L.upitch * sizeof(double), p,
+                                (size_t)c->L.nx * sizeof(double), (size_t)c->L.nx * sizeof(double), c->L.ny,
+                                cudaMemcpyHostToDevice, c->st));
+        p += N * sizeof(double);
+    }
+    c->step = h.step;
+    long long st = h.step;
+    CK(c, cudaMemcpyAsync(c->d_step, &st, sizeof st, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    return sync_status(c);
+}
+
+lbm_status lbm_info(lbm_ctx *c, int64_t *step, double *t, double *dt)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (step) *step = c->step;
+    if (t) *t = c->step * c->dt;
+    if (dt) *dt = c->dt;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (enable) clear_profile(c);
+    c->prof = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx *c, double out[4])
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->st));
+    const std::vector<cudaEvent_t> *v[2] = {&c->ev_step, &c->ev_edge};
+    for (int i = 0; i < 2; ++i) {
+        double tot = 0.0;
+        for (size_t j = 0; j + 1 < v[i]->size(); j += 2) {
+            float ms = 0.f;
+            CK(c, cudaEventElapsedTime(&ms, (*v[i])[j], (*v[i])[j + 1]));
+            tot += ms;
+        }
+        out[2 * i] = (double)(v[i]->size() / 2);
+        out[2 * i + 1] = tot;
+    }
+    return LBM_OK;
+}
+
+double lbm_bytes_per_node_update(const lbm_ctx *c)
+{
+    if (!c) return 0.0;
+    return 2.0 * 24.0 * c->eb + 4.0 * sizeof(double);
+}
+
+} // extern "C"

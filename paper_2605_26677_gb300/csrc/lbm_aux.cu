@@ -1,0 +1,343 @@
+// lbm_aux.cu -- initialization, read-out and diagnostics kernels of the TL
+// vectorial D2Q4x6 LBM. All of them compute in FP64 whatever the storage.
+#include <cfloat>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace tlv {
+
+static __device__ __forceinline__ long long pidx(const Layout &L, int q, int k, int x, int y)
+{
+    return (long long)(q * 6 + k) * L.plane + (long long)(y + 1) * L.pitch + L.xoff + x;
+}
+
+static __device__ void piola_any(int law, const double G[4], double lam, double mu, double P[4], double &dJ)
+{
+    if (law == LAW_SVK)
+        piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
+    else if (law == LAW_NH)
+        piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
+    else
+        piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
+}
+
+// Second-order difference of a compact field along x (dir 0) or y (dir 1):
+// central inside, wrap-around when periodic, one-sided three-point stencil at
+// a non-periodic end (Sec. 3.4).
+static __device__ double fd(const double *a, int nx, int ny, int x, int y, int dir, int per, double dx)
+{
+    const int n = dir == 0 ? nx : ny;
+    const int i = dir == 0 ? x : y;
+    auto at = [&](int j) { return dir == 0 ? a[(long long)y * nx + j] : a[(long long)j * nx + x]; };
+    if (per) return (at((i + 1) % n) - at((i - 1 + n) % n)) / (2.0 * dx);
+    if (i == 0) return (-3.0 * at(0) + 4.0 * at(1) - at(2)) / (2.0 * dx);
+    if (i == n - 1) return (3.0 * at(n - 1) - 4.0 * at(n - 2) + at(n - 3)) / (2.0 * dx);
+    return (at(i + 1) - at(i - 1)) / (2.0 * dx);
+}
+
+// f^eq_q(U) of Eq. (12) in full (not offset) form
+static __device__ __forceinline__ void feq_full(const double U[6], const double P[4], double c, double feq[4][6])
+{
+    const double PhiX[6] = {-P[0], -P[2], -U[0], 0.0, -U[1], 0.0};
+    const double PhiY[6] = {-P[1], -P[3], 0.0, -U[0], 0.0, -U[1]};
+    const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < 6; ++k) feq[q][k] = 0.25 * (U[k] + (2.0 / c) * (ci[q] * PhiX[k] + cj[q] * PhiY[k]));
+}
+
+// Initial populations (Sec. 3.4) followed by the collision of step 0, so the
+// stored state is f*^0; u* receives u0 - (dt/2) v0 + dt v^0 (Eq. 22).
+template <typename T>
+__global__ void __launch_bounds__(128) k_init(const InitArgs a)
+{
+    const int nx = a.L.nx, ny = a.L.ny;
+    const long long N = (long long)nx * ny;
+    T *fout = static_cast<T *>(a.fout);
+    const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
+    const double c = a.c, dt = a.dt;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        double U[6];
+        for (int k = 0; k < 6; ++k) U[k] = a.U0[k * N + n];
+        const double F[4] = {U[2], U[3], U[4], U[5]};
+        const double G[4] = {U[2] - 1.0, U[3], U[4], U[5] - 1.0};
+        double P[4], dJ, f[4][6];
+        piola_any(a.m.law, G, a.m.lam, a.m.mu, P, dJ);
+        if (!(dJ > -1.0)) atomicOr(a.status, ST_BAD_J);
+        feq_full(U, P, c, f);
+        if (a.order == 2) {
+            double gX[6], gY[6], dPX[4], dPY[4];
+            for (int k = 0; k < 6; ++k) {
+                gX[k] = fd(a.U0 + k * N, nx, ny, x, y, 0, a.xper, a.dx);
+                gY[k] = fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, a.dx);
+            }
+            // d_alpha P = C : d_alpha F (text after Eq. 18), as Jacobian actions (Eq. 8)
+            tangent_jvp(a.m.law, F, gX + 2, a.m.lam, a.m.mu, dPX);
+            tangent_jvp(a.m.law, F, gY + 2, a.m.lam, a.m.mu, dPY);
+            for (int q = 0; q < 4; ++q) {
+                const double i = ci[q], j = cj[q];
+                double Z[6], dP[4];
+                // Eq. (18): Z_q = D_q U0 with d_t U0 taken from the continuum system
+                Z[0] = a.b1 + dPX[0] + dPY[1] + c * i * gX[0] + c * j * gY[0];
+                Z[1] = a.b2 + dPX[2] + dPY[3] + c * i * gX[1] + c * j * gY[1];
+                Z[2] = gX[0] + c * i * gX[2] + c * j * gY[2];
+                Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
+                Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
+                Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
+                tangent_jvp(a.m.law, F, Z + 2, a.m.lam, a.m.mu, dP); // Eq. (20)
+                // Eq. (21): D_q f^eq = (f^eq)'(U0) Z_q, then Eq. (16)
+                const double Dq[6] = {0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1])),
+                                      0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3])),
+                                      0.25 * (Z[2] - (2.0 * i / c) * Z[0]),
+                                      0.25 * (Z[3] - (2.0 * j / c) * Z[0]),
+                                      0.25 * (Z[4] - (2.0 * i / c) * Z[1]),
+                                      0.25 * (Z[5] - (2.0 * j / c) * Z[1])};
+                for (int k = 0; k < 6; ++k) f[q][k] -= 0.5 * dt * Dq[k];
+            }
+        }
+        // step-0 collision (Eqs. 10, 12, 14)
+        double Un[6];
+        for (int k = 0; k < 6; ++k) Un[k] = f[0][k] + f[1][k] + f[2][k] + f[3][k];
+        Un[0] += 0.5 * dt * a.b1;
+        Un[1] += 0.5 * dt * a.b2;
+        const double Gn[4] = {Un[2] - 1.0, Un[3], Un[4], Un[5] - 1.0};
+        double Pn[4], feq[4][6];
+        piola_any(a.m.law, Gn, a.m.lam, a.m.mu, Pn, dJ);
+        feq_full(Un, Pn, c, feq);
+        const double src[2] = {dt * (2.0 - a.omega) * 0.125 * a.b1, dt * (2.0 - a.omega) * 0.125 * a.b2};
+        for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < 6; ++k) {
+                double fs = f[q][k] + a.omega * (feq[q][k] - f[q][k]) + (k < 2 ? src[k] : 0.0);
+                if (k == 2 || k == 5) fs -= 0.25; // store the offset from f_rest
+                fout[pidx(a.L, q, k, x, y)] = (T)fs;
+            }
+        for (int k = 0; k < 2; ++k) {
+            const double u0 = a.u0 ? a.u0[k * N + n] : 0.0;
+            a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] = (u0 - 0.5 * dt * U[k]) + dt * Un[k];
+        }
+    }
+}
+
+// U^n = sum_q f*_q - (dt/2) B, P(F^n), sigma = J^{-1} P F^T, u^n = u* - (dt/2) v^n
+// (the stored u* already holds u*^{n+1} = u*^n + dt v^n)
+template <typename T>
+__global__ void __launch_bounds__(128) k_read(const ReadArgs a)
+{
+    const int nx = a.L.nx, ny = a.L.ny;
+    const long long N = (long long)nx * ny;
+    const T *f = static_cast<const T *>(a.f);
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        double S[6];
+        for (int k = 0; k < 6; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < 4; ++q) s += (double)f[pidx(a.L, q, k, x, y)];
+            S[k] = s;
+        }
+        const double v1 = S[0] - 0.5 * a.dt * a.b1, v2 = S[1] - 0.5 * a.dt * a.b2;
+        const double G[4] = {S[2], S[3], S[4], S[5]};
+        if (a.U) {
+            a.U[0 * N + n] = v1;
+            a.U[1 * N + n] = v2;
+            a.U[2 * N + n] = 1.0 + G[0];
+            a.U[3 * N + n] = G[1];
+            a.U[4 * N + n] = G[2];
+            a.U[5 * N + n] = 1.0 + G[3];
+        }
+        if (a.P || a.sigma) {
+            double P[4], dJ;
+            piola_any(a.m.law, G, a.m.lam, a.m.mu, P, dJ);
+            if (a.P)
+                for (int m = 0; m < 4; ++m) a.P[m * N + n] = P[m];
+            if (a.sigma) {
+                const double F[4] = {1.0 + G[0], G[1], G[2], 1.0 + G[3]};
+                const double J = 1.0 + dJ;
+                a.sigma[0 * N + n] = (P[0] * F[0] + P[1] * F[1]) / J;
+                a.sigma[1 * N + n] = (P[0] * F[2] + P[1] * F[3]) / J;
+                a.sigma[2 * N + n] = (P[2] * F[0] + P[3] * F[1]) / J;
+                a.sigma[3 * N + n] = (P[2] * F[2] + P[3] * F[3]) / J;
+            }
+        }
+        if (a.u) {
+            const long long ui = (long long)y * a.L.upitch + x;
+            a.u[0 * N + n] = a.ustar[ui] - 0.5 * a.dt * v1;
+            a.u[1 * N + n] = a.ustar[a.L.uplane + ui] - 0.5 * a.dt * v2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- diagnostics
+// Ten reduced values: 7 sums (v1, v2, G11, G12, G21, G22, energy density),
+// min J, max J, max |F - I|_F. Per-block partials, then one block combines them
+// in a fixed order, so the result does not depend on scheduling.
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_MAX_BLOCKS = 1024;
+
+struct Red {
+    double s[7];
+    double jmin, jmax, gmax;
+};
+
+static __device__ __forceinline__ void red_combine(Red &r, const Red &o)
+{
+    for (int i = 0; i < 7; ++i) r.s[i] += o.s[i];
+    r.jmin = fmin(r.jmin, o.jmin);
+    r.jmax = fmax(r.jmax, o.jmax);
+    r.gmax = fmax(r.gmax, o.gmax);
+}
+
+static __device__ Red block_reduce(Red r)
+{
+    __shared__ double sh[DIAG_THREADS / 32][10];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        Red o;
+        for (int i = 0; i < 7; ++i) o.s[i] = __shfl_down_sync(0xffffffffu, r.s[i], off);
+        o.jmin = __shfl_down_sync(0xffffffffu, r.jmin, off);
+        o.jmax = __shfl_down_sync(0xffffffffu, r.jmax, off);
+        o.gmax = __shfl_down_sync(0xffffffffu, r.gmax, off);
+        red_combine(r, o);
+    }
+    if (lane == 0) {
+        for (int i = 0; i < 7; ++i) sh[w][i] = r.s[i];
+        sh[w][7] = r.jmin;
+        sh[w][8] = r.jmax;
+        sh[w][9] = r.gmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < DIAG_THREADS / 32; ++ww) {
+            Red o;
+            for (int i = 0; i < 7; ++i) o.s[i] = sh[ww][i];
+            o.jmin = sh[ww][7];
+            o.jmax = sh[ww][8];
+            o.gmax = sh[ww][9];
+            red_combine(r, o);
+        }
+    }
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const DiagArgs a)
+{
+    const int nx = a.L.nx, ny = a.L.ny;
+    const long long N = (long long)nx * ny;
+    const T *f = static_cast<const T *>(a.f);
+    Red r;
+    for (int i = 0; i < 7; ++i) r.s[i] = 0.0;
+    r.jmin = DBL_MAX;
+    r.jmax = -DBL_MAX;
+    r.gmax = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        double S[6];
+        for (int k = 0; k < 6; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < 4; ++q) s += (double)f[pidx(a.L, q, k, x, y)];
+            S[k] = s;
+        }
+        const double v1 = S[0] - 0.5 * a.dt * a.b1, v2 = S[1] - 0.5 * a.dt * a.b2;
+        const double dJ = S[2] + S[5] + (S[2] * S[5] - S[3] * S[4]);
+        r.s[0] += v1;
+        r.s[1] += v2;
+        for (int m = 0; m < 4; ++m) r.s[2 + m] += S[2 + m];
+        r.s[6] += 0.5 * (v1 * v1 + v2 * v2) + energy_ofs(a.m.law, S[2], S[3], S[4], S[5], a.m.lam, a.m.mu);
+        r.jmin = fmin(r.jmin, 1.0 + dJ);
+        r.jmax = fmax(r.jmax, 1.0 + dJ);
+        r.gmax = fmax(r.gmax, sqrt(S[2] * S[2] + S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
+    }
+    r = block_reduce(r);
+    if (threadIdx.x == 0) {
+        double *p = a.partial + (long long)blockIdx.x * 10;
+        for (int i = 0; i < 7; ++i) p[i] = r.s[i];
+        p[7] = r.jmin;
+        p[8] = r.jmax;
+        p[9] = r.gmax;
+    }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const DiagArgs a, int nblocks)
+{
+    Red r;
+    for (int i = 0; i < 7; ++i) r.s[i] = 0.0;
+    r.jmin = DBL_MAX;
+    r.jmax = -DBL_MAX;
+    r.gmax = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double *p = a.partial + (long long)b * 10;
+        Red o;
+        for (int i = 0; i < 7; ++i) o.s[i] = p[i];
+        o.jmin = p[7];
+        o.jmax = p[8];
+        o.gmax = p[9];
+        red_combine(r, o);
+    }
+    r = block_reduce(r);
+    if (threadIdx.x == 0) {
+        const double N = (double)a.L.nx * (double)a.L.ny;
+        a.out[0] = r.s[0];
+        a.out[1] = r.s[1];
+        a.out[2] = 1.0 + r.s[2] / N;
+        a.out[3] = r.s[3] / N;
+        a.out[4] = r.s[4] / N;
+        a.out[5] = 1.0 + r.s[5] / N;
+        a.out[6] = a.dx * a.dx * r.s[6];
+        a.out[7] = r.jmin;
+        a.out[8] = r.jmax;
+        a.out[9] = r.gmax;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g > 65535LL * 16) g = 65535LL * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_init(int storage_bytes, const InitArgs &a, cudaStream_t st)
+{
+    const int g = grid_for((long long)a.L.nx * a.L.ny, 128);
+    if (storage_bytes == 8)
+        k_init<double><<<g, 128, 0, st>>>(a);
+    else
+        k_init<float><<<g, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read(int storage_bytes, const ReadArgs &a, cudaStream_t st)
+{
+    const int g = grid_for((long long)a.L.nx * a.L.ny, 128);
+    if (storage_bytes == 8)
+        k_read<double><<<g, 128, 0, st>>>(a);
+    else
+        k_read<float><<<g, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int diag_blocks(const Layout &L)
+{
+    const long long n = (long long)L.nx * L.ny;
+    long long b = (n + DIAG_THREADS - 1) / DIAG_THREADS;
+    if (b > DIAG_MAX_BLOCKS) b = DIAG_MAX_BLOCKS;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_diag(int storage_bytes, const DiagArgs &a, cudaStream_t st)
+{
+    const int nb = diag_blocks(a.L);
+    if (storage_bytes == 8)
+        k_diag_partial<double><<<nb, DIAG_THREADS, 0, st>>>(a);
+    else
+        k_diag_partial<float><<<nb, DIAG_THREADS, 0, st>>>(a);
+    k_diag_final<<<1, DIAG_THREADS, 0, st>>>(a, nb);
+    return cudaGetLastError();
+}
+
+} // namespace tlv

@@ -1,0 +1,203 @@
+// lbm_device.cuh -- device-side layout, parameter blocks and pointwise
+// physics of the total-Lagrangian vectorial D2Q4x6 LBM (Feng & Chu).
+//
+// Population storage (both buffers): 24 planes p = q*6 + k (direction q of
+// Sec. 3.1, state component k of Eq. 5), each (ny + 2) rows x pitch elements.
+// Row 0 and row ny + 1 are ghost rows (y = -1, y = ny); column xoff - 1 and
+// column xoff + nx are ghost columns (x = -1, x = nx). Node (x, y) lives at
+//   p * plane + (y + 1) * pitch + xoff + x.
+// xoff is 128 bytes, so every row of real nodes starts on a 128-byte line.
+// The edge kernel writes, before each step, the value each boundary node
+// pulls from outside the domain into the ghost cell it pulls from; the bulk
+// kernel is then a uniform pull over all nodes.
+//
+// Stored values are offsets from the rest equilibrium f_rest =
+// (0, 0, 1/4, 0, 0, 1/4) (Eq. 12 at F = I, v = 0, where P(I) = 0), so the sum
+// over q of the F-components gives G = F - I directly.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tlv {
+
+enum { EDGE_LEFT = 0, EDGE_RIGHT = 1, EDGE_BOTTOM = 2, EDGE_TOP = 3 };
+enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_TRACTION = 2 };
+enum { LAW_SVK = 0, LAW_NH = 1, LAW_LOGNH = 2 };
+enum { TF_CONST = 0, TF_LINEAR_RAMP = 1, TF_SIN2_RAMP = 2, TF_SIN_PULSE = 3, TF_RICKER = 4 };
+enum { FB_NODE = 0, FB_EXTRAP2 = 1 };
+enum { ST_BAD_J = 1, ST_NEWTON = 2, ST_NONFINITE = 4 };
+
+struct Layout {
+    long long plane;  // elements per population plane
+    int pitch;        // elements per row
+    int xoff;         // column of node x = 0
+    int nx, ny;
+    long long uplane; // doubles per u* plane
+    int upitch;       // doubles per u* row (no ghost rows or columns)
+};
+
+struct Material {
+    int law;
+    double lam, mu;
+};
+
+struct EdgeDesc {
+    int kind, timefn;
+    double value[2];
+    double tp[4];
+    const double *profile; // device, one factor per edge node, or nullptr
+};
+
+template <typename T>
+struct StepArgs {
+    const T *__restrict__ fin;   // post-collision populations f*^{n-1}, ghosts filled
+    T *__restrict__ fout;        // post-collision populations f*^n
+    double *__restrict__ ustar;  // u*, advanced by dt v^n
+    int *status;                 // latched ST_* bits
+    long long *step;             // device step counter (incremented once)
+    Layout L;
+    T omega, one_m_omega, inv2c, quarter;
+    T hdtb1, hdtb2;              // (dt/2) b
+    T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
+    T lam, mu;
+    double dt;
+};
+
+struct EdgeArgs {
+    void *f;                  // populations of the current step (storage type)
+    Layout L;
+    EdgeDesc e[4];
+    int blk_end[4];           // cumulative block counts per edge
+    Material m;
+    double c, dt, dx, hdtb1, hdtb2;
+    int fb_mode, xper, yper;
+    const long long *step;
+    int *status;
+};
+
+// ---------------------------------------------------------------- pointwise
+// First Piola stress from G = F - I (Appendix A), written so that the rest
+// state does not cancel catastrophically: J - 1 = G11 + G22 + G11 G22 - G12 G21.
+// Returns J - 1 in dJ.
+template <int LAW, typename R>
+__device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, R lam, R mu, R &P11, R &P12,
+                                          R &P21, R &P22, R &dJ)
+{
+    dJ = G11 + G22 + (G11 * G22 - G12 * G21);
+    if (LAW == LAW_SVK) {
+        // Eq. (A.4): P = F S, S = lambda tr(E) I + 2 mu E, E = (G + G^T + G^T G) / 2
+        const R E11 = G11 + R(0.5) * (G11 * G11 + G21 * G21);
+        const R E22 = G22 + R(0.5) * (G12 * G12 + G22 * G22);
+        const R E12 = R(0.5) * (G12 + G21 + G11 * G12 + G21 * G22);
+        const R trE = E11 + E22;
+        const R S11 = lam * trE + R(2) * mu * E11, S22 = lam * trE + R(2) * mu * E22, S12 = R(2) * mu * E12;
+        P11 = (R(1) + G11) * S11 + G12 * S12;
+        P12 = (R(1) + G11) * S12 + G12 * S22;
+        P21 = G21 * S11 + (R(1) + G22) * S12;
+        P22 = G21 * S12 + (R(1) + G22) * S22;
+    } else {
+        // Eq. (A.5) / (A.6): P = mu (F - H) + a H, H = F^{-T} = cof(F) / J,
+        // a = (lambda/2)(J^2 - 1) (NH) or lambda log J (log-NH)
+        const R J = R(1) + dJ;
+        const R invJ = R(1) / J;
+        R a;
+        if (LAW == LAW_NH)
+            a = R(0.5) * lam * dJ * (R(2) + dJ);
+        else
+            a = lam * log1p(dJ);
+        P11 = (mu * (G11 - G22 + dJ * (R(1) + G11)) + a * (R(1) + G22)) * invJ;
+        P12 = (mu * (G12 * J + G21) - a * G21) * invJ;
+        P21 = (mu * (G21 * J + G12) - a * G12) * invJ;
+        P22 = (mu * (G22 - G11 + dJ * (R(1) + G22)) + a * (R(1) + G11)) * invJ;
+    }
+}
+
+// Strain energy W(F) of the same laws (diagnostics only), from G = F - I.
+__device__ __forceinline__ double energy_ofs(int law, double G11, double G12, double G21, double G22,
+                                             double lam, double mu)
+{
+    const double dJ = G11 + G22 + (G11 * G22 - G12 * G21);
+    if (law == LAW_SVK) {
+        const double E11 = G11 + 0.5 * (G11 * G11 + G21 * G21);
+        const double E22 = G22 + 0.5 * (G12 * G12 + G22 * G22);
+        const double E12 = 0.5 * (G12 + G21 + G11 * G12 + G21 * G22);
+        const double trE = E11 + E22;
+        return 0.5 * lam * trE * trE + mu * (E11 * E11 + 2.0 * E12 * E12 + E22 * E22);
+    }
+    // tr C - 2 = 2 (G11 + G22) + |G|^2
+    const double trCm2 = 2.0 * (G11 + G22) + G11 * G11 + G12 * G12 + G21 * G21 + G22 * G22;
+    const double lJ = log1p(dJ);
+    if (law == LAW_NH) return 0.5 * mu * (trCm2 - 2.0 * lJ) + 0.25 * lam * (dJ * (2.0 + dJ) - 2.0 * lJ);
+    return 0.5 * mu * (trCm2 - 2.0 * lJ) + 0.5 * lam * lJ * lJ;
+}
+
+// Jacobian-vector product dP = C : dF of the tangent of Eq. (4) (Eq. 8), FP64.
+__device__ __forceinline__ void tangent_jvp(int law, const double F[4], const double dF[4], double lam,
+                                            double mu, double dP[4])
+{
+    if (law == LAW_SVK) {
+        // dP = dF S + F dS, dS = lambda tr(dE) I + 2 mu dE, dE = (dF^T F + F^T dF) / 2
+        const double E11 = 0.5 * (F[0] * F[0] + F[2] * F[2] - 1.0);
+        const double E22 = 0.5 * (F[1] * F[1] + F[3] * F[3] - 1.0);
+        const double E12 = 0.5 * (F[0] * F[1] + F[2] * F[3]);
+        const double trE = E11 + E22;
+        const double S11 = lam * trE + 2.0 * mu * E11, S22 = lam * trE + 2.0 * mu * E22, S12 = 2.0 * mu * E12;
+        const double dE11 = dF[0] * F[0] + dF[2] * F[2];
+        const double dE22 = dF[1] * F[1] + dF[3] * F[3];
+        const double dE12 = 0.5 * (dF[0] * F[1] + dF[2] * F[3] + F[0] * dF[1] + F[2] * dF[3]);
+        const double dtr = dE11 + dE22;
+        const double dS11 = lam * dtr + 2.0 * mu * dE11, dS22 = lam * dtr + 2.0 * mu * dE22, dS12 = 2.0 * mu * dE12;
+        dP[0] = dF[0] * S11 + dF[1] * S12 + F[0] * dS11 + F[1] * dS12;
+        dP[1] = dF[0] * S12 + dF[1] * S22 + F[0] * dS12 + F[1] * dS22;
+        dP[2] = dF[2] * S11 + dF[3] * S12 + F[2] * dS11 + F[3] * dS12;
+        dP[3] = dF[2] * S12 + dF[3] * S22 + F[2] * dS12 + F[3] * dS22;
+        return;
+    }
+    // NH:    dP = mu dF + lambda J^2 (H : dF) H + [mu - (lambda/2)(J^2 - 1)] H dF^T H
+    // logNH: dP = mu dF + lambda     (H : dF) H + [mu - lambda log J]        H dF^T H
+    const double J = F[0] * F[3] - F[1] * F[2];
+    const double H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    const double HdF = H[0] * dF[0] + H[1] * dF[1] + H[2] * dF[2] + H[3] * dF[3];
+    double a, b;
+    if (law == LAW_NH) {
+        a = lam * J * J;
+        b = mu - 0.5 * lam * (J * J - 1.0);
+    } else {
+        a = lam;
+        b = mu - lam * log(J);
+    }
+    // (H dF^T H)_iA = sum_{B,k} H_iB dF_kB H_kA
+    double M[4];
+    for (int i = 0; i < 2; ++i)
+        for (int A = 0; A < 2; ++A) {
+            double s = 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int B = 0; B < 2; ++B) s += H[i * 2 + B] * dF[k * 2 + B] * H[k * 2 + A];
+            M[i * 2 + A] = s;
+        }
+    for (int m = 0; m < 4; ++m) dP[m] = mu * dF[m] + a * HdF * H[m] + b * M[m];
+}
+
+// Boundary-data time function g(t) (shapes of Eqs. 33, 35 and Sec. 5.4).
+__device__ __forceinline__ double timefn(int kind, const double *tp, double t)
+{
+    const double pi = 3.14159265358979323846;
+    switch (kind) {
+    case TF_CONST: return 1.0;
+    case TF_LINEAR_RAMP: return t < tp[0] ? t / tp[0] : 1.0;
+    case TF_SIN2_RAMP: {
+        if (t >= tp[0]) return 1.0;
+        const double s = sin(pi * t / (2.0 * tp[0]));
+        return s * s;
+    }
+    case TF_SIN_PULSE: return t < tp[0] ? sin(pi * t / tp[0]) : 0.0;
+    case TF_RICKER: {
+        if (t > tp[2]) return 0.0;
+        const double z = (t - tp[1]) / tp[0];
+        return 2.0 / (sqrt(3.0 * tp[0]) * pow(pi, 0.25)) * (1.0 - z * z) * exp(-0.5 * z * z);
+    }
+    default: return 0.0;
+    }
+}
+
+} // namespace tlv

@@ -1,0 +1,54 @@
+// lbm_internal.h -- host-side declarations shared by the library's
+// translation units (kernel launchers); not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace tlv {
+
+// lbm_step.cu
+cudaError_t launch_step(int storage_bytes, int law, const void *step_args, int grid, cudaStream_t st);
+cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st);
+int step_blocks_per_sm(int storage_bytes, int law);
+int step_vec(int storage_bytes);
+
+// lbm_aux.cu
+struct InitArgs {
+    const double *U0;   // 6 x N compact, device
+    const double *u0;   // 2 x N compact, device, or nullptr
+    void *fout;         // population buffer that receives f*^0
+    double *ustar;
+    int *status;
+    Layout L;
+    Material m;
+    double c, dt, dx, omega, b1, b2;
+    int order, xper, yper;
+};
+cudaError_t launch_init(int storage_bytes, const InitArgs &a, cudaStream_t st);
+
+struct ReadArgs {
+    const void *f;      // current post-collision populations
+    const double *ustar;
+    Layout L;
+    Material m;
+    double dt, b1, b2;
+    double *U;          // 6 x N or nullptr
+    double *P;          // 4 x N or nullptr
+    double *sigma;      // 4 x N or nullptr
+    double *u;          // 2 x N or nullptr
+};
+cudaError_t launch_read(int storage_bytes, const ReadArgs &a, cudaStream_t st);
+
+struct DiagArgs {
+    const void *f;
+    Layout L;
+    Material m;
+    double dt, dx, b1, b2;
+    double *partial;    // [blocks][10]
+    double *out;        // [10]
+};
+int diag_blocks(const Layout &L);
+cudaError_t launch_diag(int storage_bytes, const DiagArgs &a, cudaStream_t st);
+
+} // namespace tlv

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+include/lbm.h declares; argument checks that run before any device call."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2605_26677_gb300 import build
+
+    build.build()
+    from paper_2605_26677_gb300 import lbm as m
+
+    return m
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_set_material", "lbm_set_boundary", "lbm_init", "lbm_step",
+                     "lbm_read_state", "lbm_read_displacement", "lbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    lib = lbm.library()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(lbm.EXPORTS) == declared_functions()
+
+
+def test_library_links_no_torch(lbm):
+    # the boundary is plain C: the shared object must not depend on libtorch
+    import subprocess
+
+    out = subprocess.run(["ldd", lbm.LIB_PATH], capture_output=True, text=True).stdout
+    assert "torch" not in out and "c10" not in out
+
+
+@pytest.mark.parametrize("kw,err", [
+    (dict(nx=0, ny=8), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=0), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, omega=0.0), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, omega=2.5), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, c=-1.0), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, dx=0.0), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, storage=7), "LBM_ERR_ARG"),
+    (dict(nx=8, ny=8, storage=2), "LBM_ERR_UNSUPPORTED"),
+    (dict(nx=1 << 25, ny=8), "LBM_ERR_ARG"),
+])
+def test_create_rejects_bad_configs_before_touching_the_device(lbm, kw, err):
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(**kw)
+    assert str(ei.value).startswith(err)
+    assert lbm.lbm_last_error(None)

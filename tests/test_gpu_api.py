@@ -1,0 +1,226 @@
+"""C-ABI behaviour on the GPU: call order, argument and capacity errors, the
+latched device status (J <= 0, Newton failure, non-finite state) with the
+state still readable afterwards, device-pointer entry points, checkpoints,
+profiling counters."""
+import numpy as np
+import pytest
+
+from tests.cases import Case, run_oracle, smooth_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2605_26677_gb300 import build
+
+    build.build()
+    from paper_2605_26677_gb300 import lbm as m
+
+    return m
+
+
+def make(lbm, nx=24, ny=16, storage=1, **kw):
+    L = lbm.Lattice(nx, ny, storage=storage, **kw)
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, 0.5])
+    return L
+
+
+def rest(nx, ny):
+    U0 = np.zeros((6, ny, nx))
+    U0[2] = U0[5] = 1.0
+    return U0
+
+
+def test_call_order(lbm):
+    L = make(lbm)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_step(L.ctx, 1)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_read_state(L.ctx)
+    lbm.lbm_init(L.ctx, rest(24, 16))
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, 0.5])
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_set_body_force(L.ctx, 0.0, 1.0)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_step(L.ctx, -1)
+    lbm.lbm_step(L.ctx, 0)
+    L.close()
+    L = lbm.Lattice(8, 8)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_init(L.ctx, rest(8, 8))  # no material
+    L.close()
+
+
+def test_argument_checks(lbm):
+    L = make(lbm)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_UNSUPPORTED"):
+        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_GENT, [1.0, 0.5, 10.0])
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, -0.5])
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_set_boundary(L.ctx, 4, lbm.LBM_BC_VELOCITY)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY, (np.nan, 0.0))
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY, (0.0, 0.0), lbm.LBM_T_SIN2_RAMP, (0.0,))
+    # unpaired periodic edge
+    lbm.lbm_set_boundary(L.ctx, lbm.LBM_EDGE_LEFT, lbm.LBM_BC_VELOCITY)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_init(L.ctx, rest(24, 16))
+    lbm.lbm_set_boundary(L.ctx, lbm.LBM_EDGE_RIGHT, lbm.LBM_BC_TRACTION)
+    lbm.lbm_init(L.ctx, rest(24, 16))
+    L.close()
+    # lattice slower than the P wave: c <= sqrt(lambda + 2 mu)
+    L = lbm.Lattice(8, 8, c=1.0)
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, 0.5])
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_init(L.ctx, rest(8, 8))
+    L.close()
+    # a non-periodic direction needs three nodes
+    L = make(lbm, 2, 8)
+    lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_VELOCITY)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_init(L.ctx, rest(2, 8))
+    L.close()
+
+
+def test_out_of_memory_is_reported(lbm):
+    # 46000^2 nodes in FP64: two buffers of 24 planes need about 0.8 TB
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_OOM"):
+        lbm.lbm_create(46000, 46000, storage=lbm.LBM_STORE_F64)
+    # the device is still usable afterwards
+    L = make(lbm)
+    lbm.lbm_init(L.ctx, rest(24, 16))
+    lbm.lbm_step(L.ctx, 3)
+    L.close()
+
+
+def test_nonpositive_J_at_init(lbm):
+    L = make(lbm, 12, 10)
+    U0 = rest(12, 10)
+    U0[2, 4, 5] = -0.5  # det F < 0 at one node
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_NONPOSITIVE_J"):
+        lbm.lbm_init(L.ctx, U0)
+    # the state is readable after the error (and the latch persists)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_NONPOSITIVE_J"):
+        lbm.lbm_read_state(L.ctx)
+    lbm.lbm_init(L.ctx, rest(12, 10))  # init clears the latch
+    lbm.lbm_step(L.ctx, 2)
+    L.close()
+
+
+def test_nonfinite_state(lbm):
+    L = make(lbm, 12, 10)
+    U0 = rest(12, 10)
+    U0[0, 3, 3] = np.nan
+    lbm.lbm_init(L.ctx, U0, order=0)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_NONFINITE"):
+        lbm.lbm_step(L.ctx, 1)
+    U = np.empty((6, 10, 12))
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_NONFINITE"):
+        lbm.lbm_read_state(L.ctx, U)
+    assert np.isnan(U).any() and np.isfinite(U).any()
+    L.close()
+
+
+def test_newton_failure_on_unreachable_traction(lbm):
+    # a traction of 1e12 cannot be met within 20 damped Newton steps from F = I
+    from oracle import oracle as orc
+
+    nx, ny = 12, 10
+    L = make(lbm, nx, ny, storage=0)
+    lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_TRACTION, (1e12, 0.0))
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (1e12, 0.0))
+    lbm.lbm_init(L.ctx, rest(nx, ny))
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_NEWTON"):
+        lbm.lbm_step(L.ctx, 1)
+    L.close()
+    O = orc.Lattice(nx, ny, 1.0, 5.0, 2.0)
+    O.set_law(orc.NH, [1.0, 0.5])
+    O.set_edge(0, orc.TRACTION, (1e12, 0.0))
+    O.set_edge(1, orc.TRACTION, (1e12, 0.0))
+    O.init(rest(nx, ny))
+    O.step(1)
+    assert O.status & orc.NEWTON_FAIL
+
+
+def test_device_pointer_entry_points(lbm):
+    import torch
+
+    nx, ny = 37, 21
+    U0 = smooth_field(nx, ny, seed=2)
+    u0 = 0.1 * smooth_field(nx, ny, seed=9)[:2]
+    A = make(lbm, nx, ny, storage=0)
+    lbm.lbm_init(A.ctx, U0, u0)
+    lbm.lbm_step(A.ctx, 25)
+    U, P, _ = lbm.lbm_read_state(A.ctx)
+    u = lbm.lbm_read_displacement(A.ctx)
+    B = make(lbm, nx, ny, storage=0)
+    lbm.lbm_init_device(B.ctx, torch.from_numpy(U0).cuda(), torch.from_numpy(u0).cuda())
+    lbm.lbm_step_async(B.ctx, 25)
+    Ud = torch.empty((6, ny, nx), dtype=torch.float64, device="cuda")
+    Pd = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
+    ud = torch.empty((2, ny, nx), dtype=torch.float64, device="cuda")
+    lbm.lbm_read_state_device(B.ctx, Ud, Pd)
+    lbm.lbm_read_displacement_device(B.ctx, ud)
+    lbm.lbm_sync(B.ctx)
+    assert np.array_equal(Ud.cpu().numpy(), U)
+    assert np.array_equal(Pd.cpu().numpy(), P)
+    assert np.array_equal(ud.cpu().numpy(), u)
+    A.close()
+    B.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_checkpoint_roundtrip_is_exact(lbm, storage):
+    nx, ny = 40, 22
+    L = make(lbm, nx, ny, storage=storage)
+    lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.0), lbm.LBM_T_SIN2_RAMP, (30.0,))
+    lbm.lbm_init(L.ctx, smooth_field(nx, ny, seed=6, periodic=False))
+    lbm.lbm_step(L.ctx, 17)
+    blob = lbm.lbm_save(L.ctx)
+    lbm.lbm_step(L.ctx, 23)
+    Ua, _, ta = lbm.lbm_read_state(L.ctx)
+    ua = lbm.lbm_read_displacement(L.ctx)
+    lbm.lbm_load(L.ctx, blob)
+    assert lbm.lbm_info(L.ctx)[0] == 17
+    lbm.lbm_step(L.ctx, 23)
+    Ub, _, tb = lbm.lbm_read_state(L.ctx)
+    ub = lbm.lbm_read_displacement(L.ctx)
+    assert ta == tb and np.array_equal(Ua, Ub) and np.array_equal(ua, ub)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        lbm.lbm_load(L.ctx, blob[:100])
+    L.close()
+
+
+def test_profile_counts_launches(lbm):
+    L = make(lbm, 300, 200)
+    lbm.lbm_init(L.ctx, rest(300, 200))
+    lbm.lbm_profile(L.ctx, True)
+    lbm.lbm_step(L.ctx, 7)
+    p = lbm.lbm_profile_read(L.ctx)
+    assert p["step"][0] == 7 and p["edges"][0] == 7
+    assert p["step"][1] > 0 and p["edges"][1] > 0
+    lbm.lbm_profile(L.ctx, False)
+    assert lbm.lbm_bytes_per_node_update(L.ctx) == 224.0
+    L.close()
+
+
+def test_rest_state_is_exact_on_gpu(lbm):
+    for storage in (0, 1):
+        nx, ny = 77, 41
+        L = make(lbm, nx, ny, storage=storage)
+        for e, k in enumerate((1, 2, 2, 2)):
+            lbm.lbm_set_boundary(L.ctx, e, k)
+        lbm.lbm_init(L.ctx, rest(nx, ny))
+        lbm.lbm_step(L.ctx, 100)
+        U, P, _ = lbm.lbm_read_state(L.ctx)
+        assert np.array_equal(U, rest(nx, ny)) and not P.any()
+        L.close()
