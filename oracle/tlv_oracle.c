@@ -448,13 +448,10 @@ static double fd(const orc *o, const double *a, int ix, int iy, int dir)
 
 static int check_edges(const orc *o)
 {
-    int e;
     if ((o->e[ORC_LEFT].kind == ORC_PERIODIC) != (o->e[ORC_RIGHT].kind == ORC_PERIODIC)) return -2;
     if ((o->e[ORC_BOTTOM].kind == ORC_PERIODIC) != (o->e[ORC_TOP].kind == ORC_PERIODIC)) return -2;
     if (!xper(o) && o->nx < 3) return -3;
     if (!yper(o) && o->ny < 3) return -3;
-    for (e = 0; e < 4; ++e)
-        if (o->e[e].kind == ORC_TRACTION && edge_len(o, e) < 3) return -3;
     return 0;
 }
 

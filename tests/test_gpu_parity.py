@@ -4,7 +4,11 @@ tail, for every edge rule, closure, storage precision and degenerate size.
 
 Tolerances (relative L2 per group; groups are v, F - I, P, u, sigma and the
 full state U over all nodes and components):
-  FP64 storage: 1e-12.
+  FP64 storage: 1e-12 on U; 1e-11 per group. The 64^2 shear wave is neutral
+  (omega = 2) for 1000 steps, and perturbing its initial state by one ulp
+  moves the oracle's own v, P and F - I by 3.5e-12, 1.7e-12 and 8e-13
+  (test_oracle_conditioning); the per-group bound sits a factor three above
+  that floor.
   FP32 storage: 1e-5 on U (the paper's full-state norm); 1e-4 per group. Per
   step each stored value is rounded once in FP32 (eps = 6e-8) and about ten
   operations touch it, so a neutral (omega = 2) scheme accumulates about
@@ -19,7 +23,7 @@ from tests.cases import Case, group_errors, run_gpu, run_oracle, smooth_field
 pytestmark = pytest.mark.gpu
 
 F64, F32 = 0, 1
-TOL = {F64: dict(group=1e-12, U=1e-12), F32: dict(group=1e-4, U=1e-5)}
+TOL = {F64: dict(group=1e-11, U=1e-12), F32: dict(group=1e-4, U=1e-5)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -132,10 +136,16 @@ def test_initialization_only(order, edges):
     U0 = smooth_field(nx, ny, seed=3, amp=0.05, periodic=(edges == "periodic"))
     u0 = 0.01 * smooth_field(nx, ny, seed=4)[:2]
     case = Case(nx, ny, 0, order=order, body=(0.01, -0.02), edges=E, U0=U0, u0=u0)
-    errs = check(case, F64)
-    # zero steps: the recovered state is U0 itself (Eq. 10 with Eq. 16 summed over q)
+    check(case, F64)
+    # zero steps: Eq. (10) with Eq. (16) summed over q gives U0 for the
+    # second-order start; the equilibrium start has sum_q f = U0, so Eq. (10)
+    # adds (dt/2) B to the velocity
     g = run_gpu(case, F64)
-    assert np.abs(g["U"] - U0).max() < 1e-14
+    expect = U0.copy()
+    if order == 0:
+        expect[0] += 0.5 * 0.2 * 0.01
+        expect[1] += 0.5 * 0.2 * -0.02
+    assert np.abs(g["U"] - expect).max() < 1e-14
     assert np.abs(g["u"] - u0).max() < 1e-15
 
 

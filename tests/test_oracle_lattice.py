@@ -248,3 +248,28 @@ def test_traction_edge_stability_threshold():
     other three, NH lambda = 2, mu = 1, c = 5."""
     assert _seeded_growth(1.95, 2000) < 1e-11
     assert _seeded_growth(2.0, 1200) > 1e-9
+
+
+def test_oracle_conditioning_of_the_64_shear_wave():
+    """The floor any FP64 comparison of the 64 x 64 shear wave (1000 steps,
+    omega = 2) can reach: perturbing the initial state by one ulp moves the
+    oracle's own result by about 3.5e-12 in v and 1.7e-12 in P, 7e-15 in U."""
+    from synth import shear_wave_64
+    from tests.cases import group_errors
+
+    w = shear_wave_64()
+    U0, u0 = w.fields()
+
+    def run(U):
+        L = o.Lattice(64, 64, 1.0, 5.0, 2.0)
+        L.set_law(o.NH, [1.0, 0.5])
+        L.init(U, u0, 2)
+        L.step(1000)
+        U1, P1, S1 = L.state()
+        return {"U": U1, "P": P1, "u": L.displacement(), "sigma": S1}
+
+    a = run(U0)
+    rng = np.random.default_rng(0)
+    b = run(U0 * (1 + 2.2e-16 * rng.choice([-1, 1], size=U0.shape)))
+    e = group_errors(a, b)
+    assert 1e-12 < e["v"] < 1e-11 and 5e-13 < e["P"] < 5e-12 and e["U"] < 1e-13, e
