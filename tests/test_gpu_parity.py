@@ -146,7 +146,8 @@ def test_initialization_only(order, edges):
         expect[0] += 0.5 * 0.2 * 0.01
         expect[1] += 0.5 * 0.2 * -0.02
     assert np.abs(g["U"] - expect).max() < 1e-14
-    assert np.abs(g["u"] - u0).max() < 1e-15
+    # u^0 = u*^0 + (dt/2) v^0 with u*^0 = u0 - (dt/2) v0 (Eq. 22)
+    assert np.abs(g["u"] - (u0 + 0.1 * (expect[:2] - U0[:2]))).max() < 1e-15
 
 
 @pytest.mark.parametrize("order", [0, 2])
