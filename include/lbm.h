@@ -121,8 +121,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
  * context's stream. */
 void lbm_destroy(lbm_ctx *ctx);
 
-/* Text of the last error on ctx (or of the last failed lbm_create on this
- * host thread when ctx is NULL). Valid until the next call on ctx. */
+/* Text of the last error on ctx (or, when ctx is NULL, of the last failed
+ * call on this host thread that takes no context: lbm_create or
+ * lbm_diagnostics_state_noalloc). Valid until the next call on ctx. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
 /* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A). Must be
@@ -207,6 +208,26 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double out[4]);
  * HBM for this context's storage (populations read and written, u* read and
  * written). */
 double lbm_bytes_per_node_update(const lbm_ctx *ctx);
+
+/* Diagnostics of a state field without allocating device memory. The paper
+ * has no counterpart; this entry point exists for callers that cannot let a
+ * library call cudaMalloc -- applications that give out all device memory
+ * from their own pool, or loops that must not pay for or be serialised by an
+ * allocation. It reduces the caller's FP64 state U_dev (device, 6N,
+ * component-major v1, v2, F11, F12, F21, F22; e.g. from
+ * lbm_read_state_device) into the caller's out_dev (device, 10 doubles, the
+ * layout of lbm_diagnostics) for closure `law` (SVK, NH, LOGNH) with params
+ * {lambda, mu} and spacing dx, on `stream` of `device`, without waiting.
+ * Its block partials live in one fixed 1.25 MiB array in the library's device
+ * memory (held on every GPU that loads the library until the process exits),
+ * so a call takes at most 67,108,864 nodes (8192^2) and returns LBM_ERR_ARG
+ * beyond that. The first call on a device looks the array's address up; make
+ * that first call before any stream capture. Calls share the array, so calls
+ * whose kernels overlap on the GPU race with each other. Errors are reported
+ * by lbm_last_error(NULL). */
+lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t nx, int32_t ny, int32_t law,
+                                         const double *params, int32_t nparams, double dx, double *out_dev,
+                                         int32_t device, void *stream);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,8 @@ struct lbm_ctx {
 
 static thread_local std::string g_create_err;
 
+void tlv::set_thread_error(const std::string &msg) { g_create_err = msg; }
+
 namespace {
 
 lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg)

@@ -1,6 +1,8 @@
 // lbm_internal.h -- host-side declarations shared by the library's
 // translation units (kernel launchers); not part of the public C ABI.
 #pragma once
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -50,5 +52,8 @@ struct DiagArgs {
 };
 int diag_blocks(const Layout &L);
 cudaError_t launch_diag(int storage_bytes, const DiagArgs &a, cudaStream_t st);
+
+// lbm_api.cu: message returned by lbm_last_error(NULL) on this host thread
+void set_thread_error(const std::string &msg);
 
 } // namespace tlv

@@ -30,7 +30,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "l
            "lbm_set_boundary", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
            "lbm_read_state", "lbm_read_state_device", "lbm_read_displacement", "lbm_read_displacement_device",
            "lbm_read_cauchy", "lbm_diagnostics", "lbm_save", "lbm_load", "lbm_info", "lbm_profile",
-           "lbm_profile_read", "lbm_bytes_per_node_update"]
+           "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc"]
 
 
 class lbm_config(C.Structure):
@@ -88,6 +88,8 @@ _lib.lbm_profile.argtypes = [_ctx, C.c_int32]
 _lib.lbm_profile_read.argtypes = [_ctx, _dp]
 _lib.lbm_bytes_per_node_update.argtypes = [_ctx]
 _lib.lbm_bytes_per_node_update.restype = C.c_double
+_lib.lbm_diagnostics_state_noalloc.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int32,
+                                               C.c_double, C.c_void_p, C.c_int32, C.c_void_p]
 
 
 def library():
@@ -287,6 +289,21 @@ def lbm_profile_read(ctx):
 
 def lbm_bytes_per_node_update(ctx):
     return _lib.lbm_bytes_per_node_update(ctx)
+
+
+def lbm_diagnostics_state_noalloc(U_dev, nx, ny, law, params, dx, out_dev, device=0, stream=None):
+    """U_dev: (6, ny, nx) float64 CUDA tensor; out_dev: 10-element float64 CUDA
+    tensor. Enqueued on `stream` (default: torch's current stream)."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream(device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    p = np.asarray(params, dtype=np.float64)
+    st = _lib.lbm_diagnostics_state_noalloc(_dev(U_dev, 6 * nx * ny), nx, ny, law, p.ctypes.data_as(_dp), len(p),
+                                            dx, _dev(out_dev, 10), device, C.c_void_p(stream or None))
+    _check(None, st)
 
 
 # ---------------------------------------------------------------- helper
