@@ -23,7 +23,7 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     double *ustar = nullptr;
     int *d_status = nullptr;
-    long long *d_step = nullptr;
+    long long *d_step = nullptr; // [2]: steps completed, one slot per buffer parity
     double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
     double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
     int cur = 0;
@@ -34,6 +34,7 @@ struct lbm_ctx {
     double b[2] = {0.0, 0.0};
     EdgeDesc edge[4]{};
     bool initialized = false;
+    bool ghosts_dirty = true;  // ghost cells of f[cur] must be rebuilt before the next step
     int grid_step = 1;
     int edge_blk_end[4] = {0, 0, 0, 0};
     std::string err;
@@ -114,7 +115,8 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.fout = static_cast<T *>(c->f[cur ^ 1]);
     a.ustar = c->ustar;
     a.status = c->d_status;
-    a.step = c->d_step;
+    a.step_in = c->d_step + cur;
+    a.step_out = c->d_step + (cur ^ 1);
     a.L = c->L;
     const double w = c->cfg.omega;
     a.omega = (T)w;
@@ -127,7 +129,16 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.src2 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[1]);
     a.lam = (T)c->m.lam;
     a.mu = (T)c->m.mu;
+    a.c = (T)c->cfg.c;
     a.dt = c->dt;
+    for (int e = 0; e < 4; ++e) {
+        a.kind[e] = c->edge[e].kind;
+        a.timefn[e] = c->edge[e].timefn;
+        a.value[e][0] = c->edge[e].value[0];
+        a.value[e][1] = c->edge[e].value[1];
+        for (int i = 0; i < 4; ++i) a.tp[e][i] = c->edge[e].tp[i];
+        a.profile[e] = c->edge[e].profile;
+    }
     return a;
 }
 
@@ -149,7 +160,7 @@ EdgeArgs edge_args(const lbm_ctx *c, int cur)
     a.fb_mode = c->cfg.fb_mode;
     a.xper = xper(c);
     a.yper = yper(c);
-    a.step = c->d_step;
+    a.step = c->d_step + cur;
     a.status = c->d_status;
     return a;
 }
@@ -171,18 +182,29 @@ lbm_status record(lbm_ctx *c, std::vector<cudaEvent_t> &v)
     return LBM_OK;
 }
 
+// In the node form of F^b every ghost value depends only on its own boundary
+// node, so the step kernel writes the next step's ghosts itself (fused) and
+// the separate ghost kernel runs only when they are stale. The extrapolated
+// form needs neighbouring nodes and keeps the edge kernel before every step.
 template <typename T>
 lbm_status do_step(lbm_ctx *c, int64_t nsteps)
 {
     const bool prof = c->prof && (c->ev_step.size() < 200000);
+    const bool fuse = c->cfg.fb_mode == LBM_FB_NODE;
     for (int64_t i = 0; i < nsteps; ++i) {
-        const EdgeArgs ea = edge_args(c, c->cur);
-        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
-        CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
-        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+        if (!fuse || c->ghosts_dirty) {
+            const EdgeArgs ea = edge_args(c, c->cur);
+            if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+            if (fuse)
+                CK(c, launch_ghosts(c->eb, ea, c->edge_blk_end[3], c->st));
+            else
+                CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
+            if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+            c->ghosts_dirty = false;
+        }
         const StepArgs<T> sa = step_args<T>(c, c->cur);
         if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
-        CK(c, launch_step(c->eb, c->m.law, &sa, c->grid_step, c->st));
+        CK(c, launch_step(c->eb, c->m.law, fuse, &sa, c->grid_step, c->st));
         if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
         c->cur ^= 1;
         c->step += 1;
@@ -237,6 +259,56 @@ struct SaveHeader {
     int32_t version, nx, ny, eb;
     int64_t step;
 };
+
+// Ghost cells of the current buffer (what the boundary nodes pull at the next
+// step): left/right columns of planes q = 0 / 2 and bottom/top rows of planes
+// q = 1 / 3, six components each. Checkpoints carry them so that a resumed
+// run continues bit for bit.
+size_t ghost_elems(const lbm_ctx *c) { return (size_t)12 * ((size_t)c->L.nx + c->L.ny); }
+
+lbm_status copy_ghosts(lbm_ctx *c, char *host, bool to_host)
+{
+    char *base = static_cast<char *>(c->f[c->cur]);
+    const size_t eb = c->eb, pitchb = (size_t)c->L.pitch * eb;
+    const int nx = c->L.nx, ny = c->L.ny;
+    for (int e = 0; e < 4; ++e) {
+        const int q = (e == EDGE_LEFT) ? 0 : (e == EDGE_RIGHT) ? 2 : (e == EDGE_BOTTOM) ? 1 : 3;
+        for (int k = 0; k < 6; ++k) {
+            const size_t plane = (size_t)(q * 6 + k) * c->L.plane;
+            size_t off, width, height, spitch;
+            if (e <= EDGE_RIGHT) {  // one column, ny rows
+                off = plane + c->L.pitch + c->L.xoff + (e == EDGE_LEFT ? -1 : nx);
+                width = eb;
+                height = ny;
+                spitch = pitchb;
+            } else {                // one row of nx nodes
+                off = plane + (size_t)(e == EDGE_BOTTOM ? 0 : ny + 1) * c->L.pitch + c->L.xoff;
+                width = (size_t)nx * eb;
+                height = 1;
+                spitch = width;
+            }
+            char *dev = base + off * eb;
+            if (to_host)
+                CK(c, cudaMemcpy2DAsync(host, width, dev, spitch, width, height, cudaMemcpyDeviceToHost, c->st));
+            else
+                CK(c, cudaMemcpy2DAsync(dev, spitch, host, width, width, height, cudaMemcpyHostToDevice, c->st));
+            host += width * height;
+        }
+    }
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status refresh_ghosts(lbm_ctx *c)
+{
+    const EdgeArgs ea = edge_args(c, c->cur);
+    if (c->cfg.fb_mode == LBM_FB_NODE)
+        CK(c, launch_ghosts(c->eb, ea, c->edge_blk_end[3], c->st));
+    else
+        CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
+    c->ghosts_dirty = false;
+    return LBM_OK;
+}
 
 } // namespace
 
@@ -305,13 +377,13 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     CKC(cudaMalloc(&c->f[1], fbytes));
     CKC(cudaMalloc((void **)&c->ustar, ubytes));
     CKC(cudaMalloc((void **)&c->d_status, sizeof(int)));
-    CKC(cudaMalloc((void **)&c->d_step, sizeof(long long)));
+    CKC(cudaMalloc((void **)&c->d_step, 2 * sizeof(long long)));
     CKC(cudaMalloc((void **)&c->d_diag, (size_t)(diag_blocks(c->L) * 10 + 10) * sizeof(double)));
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->ustar, 0, ubytes, c->st));
     CKC(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
-    CKC(cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->st));
+    CKC(cudaMemsetAsync(c->d_step, 0, 2 * sizeof(long long), c->st));
     CKC(cudaStreamSynchronize(c->st));
 #undef CKC
     int sms = 0;
@@ -411,6 +483,7 @@ lbm_status lbm_set_boundary(lbm_ctx *c, int32_t edge, int32_t bc, const double v
         d.profile = nullptr;
     }
     c->edge[edge] = d;
+    c->ghosts_dirty = true;
     return LBM_OK;
 }
 
@@ -434,11 +507,12 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     a.xper = xper(c);
     a.yper = yper(c);
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
-    CK(c, cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->st));
+    CK(c, cudaMemsetAsync(c->d_step, 0, 2 * sizeof(long long), c->st));
     CK(c, launch_init(c->eb, a, c->st));
     c->cur = 0;
     c->step = 0;
     c->initialized = true;
+    c->ghosts_dirty = true;
     return LBM_OK;
 }
 
@@ -587,15 +661,19 @@ lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
     if (s != LBM_OK) return s;
     if (!bytes) return fail(c, LBM_ERR_ARG, "bytes is NULL");
     const size_t N = (size_t)c->L.nx * c->L.ny;
-    const size_t need = sizeof(SaveHeader) + 24 * N * c->eb + 2 * N * sizeof(double);
+    const size_t need = sizeof(SaveHeader) + 24 * N * c->eb + 2 * N * sizeof(double) + ghost_elems(c) * c->eb;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
     }
     if (*bytes < need) return fail(c, LBM_ERR_ARG, "buffer too small");
+    if (c->ghosts_dirty) {
+        s = (c->eb == 8) ? refresh_ghosts<double>(c) : refresh_ghosts<float>(c);
+        if (s != LBM_OK) return s;
+    }
     SaveHeader h{};
-    std::memcpy(h.magic, "TLVLBM01", 8);
-    h.version = 1;
+    std::memcpy(h.magic, "TLVLBM02", 8);
+    h.version = 2;
     h.nx = c->L.nx;
     h.ny = c->L.ny;
     h.eb = c->eb;
@@ -615,6 +693,8 @@ lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
                                 cudaMemcpyDeviceToHost, c->st));
         p += N * sizeof(double);
     }
+    s = copy_ghosts(c, p, true);
+    if (s != LBM_OK) return s;
     *bytes = need;
     return sync_status(c);
 }
@@ -627,10 +707,11 @@ lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
     SaveHeader h;
     std::memcpy(&h, buf, sizeof h);
     const size_t N = (size_t)c->L.nx * c->L.ny;
-    if (std::memcmp(h.magic, "TLVLBM01", 8) != 0 || h.version != 1) return fail(c, LBM_ERR_ARG, "not a checkpoint");
+    if (std::memcmp(h.magic, "TLVLBM02", 8) != 0 || h.version != 2) return fail(c, LBM_ERR_ARG, "not a checkpoint");
     if (h.nx != c->L.nx || h.ny != c->L.ny || h.eb != c->eb)
         return fail(c, LBM_ERR_ARG, "checkpoint grid or storage differs from the context");
-    if (bytes < sizeof h + 24 * N * c->eb + 2 * N * sizeof(double)) return fail(c, LBM_ERR_ARG, "truncated checkpoint");
+    if (bytes < sizeof h + 24 * N * c->eb + 2 * N * sizeof(double) + ghost_elems(c) * c->eb)
+        return fail(c, LBM_ERR_ARG, "truncated checkpoint");
     CK(c, cudaStreamSynchronize(c->st));
     const char *p = static_cast<const char *>(buf) + sizeof h;
     const size_t rowb = (size_t)c->L.nx * c->eb;
@@ -646,9 +727,12 @@ lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
                                 cudaMemcpyHostToDevice, c->st));
         p += N * sizeof(double);
     }
+    s = copy_ghosts(c, const_cast<char *>(p), false);
+    if (s != LBM_OK) return s;
     c->step = h.step;
-    long long st = h.step;
-    CK(c, cudaMemcpyAsync(c->d_step, &st, sizeof st, cudaMemcpyHostToDevice, c->st));
+    c->ghosts_dirty = false;
+    const long long st[2] = {h.step, h.step};
+    CK(c, cudaMemcpyAsync(c->d_step, st, sizeof st, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
     return sync_status(c);
 }

@@ -54,13 +54,18 @@ struct StepArgs {
     T *__restrict__ fout;        // post-collision populations f*^n
     double *__restrict__ ustar;  // u*, advanced by dt v^n
     int *status;                 // latched ST_* bits
-    long long *step;             // device step counter (incremented once)
+    const long long *step_in;    // steps completed before this launch (n - 1)
+    long long *step_out;         // receives n (the other slot of a ping-pong pair)
     Layout L;
     T omega, one_m_omega, inv2c, quarter;
     T hdtb1, hdtb2;              // (dt/2) b
     T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
-    T lam, mu;
+    T lam, mu, c;
     double dt;
+    // edge rules, used when the kernel also writes the ghost cells of fout
+    int kind[4], timefn[4];
+    double value[4][2], tp[4][4];
+    const double *profile[4];
 };
 
 struct EdgeArgs {

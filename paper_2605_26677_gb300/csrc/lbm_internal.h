@@ -10,8 +10,12 @@
 namespace tlv {
 
 // lbm_step.cu
-cudaError_t launch_step(int storage_bytes, int law, const void *step_args, int grid, cudaStream_t st);
+// fuse: the step kernel also writes the next step's ghost cells (node form)
+cudaError_t launch_step(int storage_bytes, int law, bool fuse, const void *step_args, int grid, cudaStream_t st);
+// ghost cells of the current buffer: k_edges (either F^b form, FP64 Newton)
+// and k_ghosts (node form, the fused kernel's arithmetic)
 cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_ghosts(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st);
 int step_blocks_per_sm(int storage_bytes, int law);
 int step_vec(int storage_bytes);
 

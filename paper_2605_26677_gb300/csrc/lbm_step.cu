@@ -12,6 +12,7 @@
 // The stored state between steps is the post-collision f*^n, so streaming
 // (Eq. 15) happens at the start of the next step as a pull.
 #include "lbm_device.cuh"
+#include "lbm_edges.cuh"
 #include "lbm_internal.h"
 
 namespace tlv {
@@ -30,7 +31,25 @@ struct alignas(sizeof(T) * N) Pack {
 // loads); the +x and -x populations come from the same row shifted by one
 // column: each lane loads its own aligned vector and takes the missing end
 // element from its neighbour lane by a shuffle (lane 0 / lane 31 load it).
-template <typename T, int LAW, int VEC>
+//
+// With FUSE the kernel also writes, into the ghost cells of fout, what the
+// boundary nodes pull at the next step: everything that value depends on in
+// the node form of Sec. 3.6 (f*_{-d} and U^n of the boundary node itself) is
+// in the registers of the thread that owns the node. Periodic ghosts are the
+// outgoing populations of the opposite edge's nodes.
+
+// U^n of a node from its post-collision populations: sum_q f*_q = U + (dt/2) B
+template <typename T>
+__device__ __forceinline__ void state_from_fstar(const T f0[6], const T f1[6], const T f2[6], const T f3[6], T hb1,
+                                                 T hb2, T U[6])
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U[k] = (f0[k] + f2[k]) + (f1[k] + f3[k]);
+    U[0] -= hb1;
+    U[1] -= hb2;
+}
+
+template <typename T, int LAW, int VEC, bool FUSE>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
 {
     using PK = Pack<T, VEC>;
@@ -39,21 +58,26 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
     const int wpb = blockDim.x >> 5;
     const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * wpb;
-    const int nx = a.L.nx;
+    const int nx = a.L.nx, ny = a.L.ny;
     const int segw = 32 * VEC;
     const int nseg = (nx + segw - 1) / segw;
-    const long long ntask = (long long)a.L.ny * nseg;
+    const long long ntask = (long long)ny * nseg;
     const long long plane = a.L.plane;
     const int pitch = a.L.pitch;
     const T *__restrict__ fin = a.fin;
     T *__restrict__ fout = a.fout;
-
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step += 1;
+    const long long n_in = *a.step_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step_out = n_in + 1;
+    // edge data for the next step's pull is sampled at t^{n} + dt/2 (Eq. 23)
+    const double th = ((double)n_in + 1.5) * a.dt;
 
     unsigned flags = 0;
     for (long long task = gw; task < ntask; task += nw) {
         const int y = (int)(task / nseg);
-        const int seg = (int)(task - (long long)y * nseg);
+        // the segments of row y are taken in an order rotated by y: with a warp
+        // count that is a multiple of nseg, an unrotated order would give every
+        // edge segment (and its Newton solves) to the same few warps
+        const int seg = (int)((task - (long long)y * nseg + y) % nseg);
         const int x0 = seg * segw + lane * VEC;
         const bool act = x0 < nx;   // lane owns at least one real node
         const bool ld0 = x0 <= nx;  // lane's vector holds a real node or the right ghost column
@@ -118,14 +142,23 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
         }
 
         if (act) {
+            const bool full = x0 + VEC <= nx;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    PK o;
+                    T *dst = fout + (q * 6 + k) * plane + row;
+                    if (full) {
+                        PK o;
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) o.v[e] = f[q][k][e];
-                    *reinterpret_cast<PK *>(fout + (q * 6 + k) * plane + row) = o;
+                        for (int e = 0; e < VEC; ++e) o.v[e] = f[q][k][e];
+                        *reinterpret_cast<PK *>(dst) = o;
+                    } else {
+                        // ragged end: never write past node nx - 1 (column nx is a ghost cell)
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (x0 + e < nx) dst[e] = f[q][k][e];
+                    }
                 }
             // Eq. (22): u*^{n+1} = u*^n + dt v^n (the two half steps of the paper)
             const long long urow = (long long)y * a.L.upitch + x0;
@@ -136,10 +169,158 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
                 for (int e = 0; e < VEC; ++e) u.v[e] += a.dt * (double)vel[c][e];
                 *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
             }
+
+            if (FUSE) {
+                // ---- bottom ghost row (plane q=1, row y = -1) and top ghost row
+                // (plane q=3, row y = ny): whole vectors, one per lane
+                const bool ypers = a.kind[EDGE_BOTTOM] == BC_PERIODIC;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int e_id = side == 0 ? EDGE_BOTTOM : EDGE_TOP;
+                    const int qd = side == 0 ? 1 : 3;          // missing direction
+                    const int qo = side == 0 ? 3 : 1;          // outgoing direction -d
+                    const int yb = side == 0 ? 0 : ny - 1;     // boundary row
+                    const int ysrc = side == 0 ? ny - 1 : 0;   // periodic source row
+                    const long long grow = (long long)(side == 0 ? 0 : ny + 1) * pitch + a.L.xoff + x0;
+                    T *dst = fout + (long long)(qd * 6) * plane + grow;
+                    if (ypers) {
+                        if (y == ysrc)
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) {
+                                PK o;
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) o.v[e] = f[qd][k][e];
+                                *reinterpret_cast<PK *>(dst + k * plane) = o;
+                            }
+                    } else if (y == yb) {
+                        T g[6][VEC];
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) {
+                            T out[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                            if (x0 + e < nx) {
+                                T fo[6], f0[6], f1[6], f2[6], f3[6], U[6];
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) {
+                                    fo[k] = f[qo][k][e];
+                                    f0[k] = f[0][k][e]; f1[k] = f[1][k][e]; f2[k] = f[2][k][e]; f3[k] = f[3][k][e];
+                                }
+                                state_from_fstar(f0, f1, f2, f3, a.hdtb1, a.hdtb2, U);
+                                double val[2];
+                                const double gt = timefn(a.timefn[e_id], a.tp[e_id], th) *
+                                                  (a.profile[e_id] ? a.profile[e_id][x0 + e] : 1.0);
+                                val[0] = a.value[e_id][0] * gt;
+                                val[1] = a.value[e_id][1] * gt;
+                                edge_ghost<LAW, T>(e_id, a.kind[e_id], fo, U, val, a.c, a.lam, a.mu, out, flags);
+                            }
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) g[k][e] = out[k];
+                        }
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            PK o;
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) o.v[e] = g[k][e];
+                            *reinterpret_cast<PK *>(dst + k * plane) = o;
+                        }
+                    }
+                }
+                // ---- left ghost column (plane 0, x = -1) and right ghost column
+                // (plane 2, x = nx): one element of one lane per row
+                const bool xpers = a.kind[EDGE_LEFT] == BC_PERIODIC;
+                const long long rbase = (long long)(y + 1) * pitch + a.L.xoff;
+                const int elast = nx - 1 - x0;  // element of node nx - 1 in this lane, if any
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int e_id = side == 0 ? EDGE_LEFT : EDGE_RIGHT;
+                    const int qd = side == 0 ? 0 : 2, qo = side == 0 ? 2 : 0;
+                    const int gx = side == 0 ? -1 : nx;
+                    // element holding the boundary node (left: x = 0, right: x = nx-1)
+                    // and, for periodic edges, the source node on the opposite side
+                    const int eb = side == 0 ? (x0 == 0 ? 0 : -1) : (elast >= 0 && elast < VEC ? elast : -1);
+                    const int es = side == 0 ? (elast >= 0 && elast < VEC ? elast : -1) : (x0 == 0 ? 0 : -1);
+                    T *dst = fout + (long long)(qd * 6) * plane + rbase + gx;
+                    if (xpers) {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (e == es)
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) dst[k * plane] = f[qd][k][e];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (e == eb) {
+                                T fo[6], f0[6], f1[6], f2[6], f3[6], U[6], out[6];
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) {
+                                    fo[k] = f[qo][k][e];
+                                    f0[k] = f[0][k][e]; f1[k] = f[1][k][e]; f2[k] = f[2][k][e]; f3[k] = f[3][k][e];
+                                }
+                                state_from_fstar(f0, f1, f2, f3, a.hdtb1, a.hdtb2, U);
+                                double val[2];
+                                const double gt = timefn(a.timefn[e_id], a.tp[e_id], th) *
+                                                  (a.profile[e_id] ? a.profile[e_id][y] : 1.0);
+                                val[0] = a.value[e_id][0] * gt;
+                                val[1] = a.value[e_id][1] * gt;
+                                edge_ghost<LAW, T>(e_id, a.kind[e_id], fo, U, val, a.c, a.lam, a.mu, out, flags);
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) dst[k * plane] = out[k];
+                            }
+                    }
+                }
+            }
         }
     }
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
+}
+
+// Ghost refresh in the node form (after initialization, a checkpoint load or
+// new edge data): the same values the fused step writes, from the stored
+// post-collision populations of the current buffer.
+template <typename T, int LAW>
+__global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
+{
+    T *f = static_cast<T *>(a.f);
+    int e = 0;
+    while (e < 3 && (int)blockIdx.x >= a.blk_end[e]) ++e;
+    const int b0 = e ? a.blk_end[e - 1] : 0;
+    const int s = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x;
+    const int len = (e <= EDGE_RIGHT) ? a.L.ny : a.L.nx;
+    if (s >= len) return;
+    auto idx = [&](int q, int k, int x, int y) {
+        return (long long)(q * 6 + k) * a.L.plane + (long long)(y + 1) * a.L.pitch + a.L.xoff + x;
+    };
+    int xb, yb, gx, gy;
+    switch (e) {
+    case EDGE_LEFT: xb = 0; yb = s; gx = -1; gy = s; break;
+    case EDGE_RIGHT: xb = a.L.nx - 1; yb = s; gx = a.L.nx; gy = s; break;
+    case EDGE_BOTTOM: xb = s; yb = 0; gx = s; gy = -1; break;
+    default: xb = s; yb = a.L.ny - 1; gx = s; gy = a.L.ny; break;
+    }
+    const int d = edge_dmiss(e), md = edge_dout(e);
+    const EdgeDesc &E = a.e[e];
+    if (E.kind == BC_PERIODIC) {
+        const int sx = (e == EDGE_LEFT) ? a.L.nx - 1 : (e == EDGE_RIGHT) ? 0 : s;
+        const int sy = (e == EDGE_BOTTOM) ? a.L.ny - 1 : (e == EDGE_TOP) ? 0 : s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = f[idx(d, k, sx, sy)];
+        return;
+    }
+    T fq[4][6], U[6], fo[6], out[6];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fq[q][k] = f[idx(q, k, xb, yb)];
+    state_from_fstar(fq[0], fq[1], fq[2], fq[3], (T)a.hdtb1, (T)a.hdtb2, U);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fo[k] = fq[md][k];
+    double val[2];
+    edge_value(E, s, ((double)(*a.step) + 0.5) * a.dt, val);
+    unsigned flags = 0;
+    edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, (T)a.m.lam, (T)a.m.mu, out, flags);
+    if (flags) atomicOr(a.status, (int)flags);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = out[k];
 }
 
 // ---------------------------------------------------------------- edges
@@ -364,27 +545,31 @@ __global__ void __launch_bounds__(128) k_edges(const EdgeArgs a)
 
 // ---------------------------------------------------------------- launchers
 template <typename T, int LAW, int VEC>
-static cudaError_t launch_step_t(const StepArgs<T> &a, int grid, cudaStream_t st)
+static cudaError_t launch_step_t(const StepArgs<T> &a, bool fuse, int grid, cudaStream_t st)
 {
-    k_step<T, LAW, VEC><<<grid, 128, 0, st>>>(a);
+    if (fuse)
+        k_step<T, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
+    else
+        k_step<T, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_step_law(int law, const StepArgs<T> &a, int grid, cudaStream_t st)
+static cudaError_t launch_step_law(int law, const StepArgs<T> &a, bool fuse, int grid, cudaStream_t st)
 {
     constexpr int VEC = 16 / sizeof(T);
     switch (law) {
-    case LAW_SVK: return launch_step_t<T, LAW_SVK, VEC>(a, grid, st);
-    case LAW_NH: return launch_step_t<T, LAW_NH, VEC>(a, grid, st);
-    default: return launch_step_t<T, LAW_LOGNH, VEC>(a, grid, st);
+    case LAW_SVK: return launch_step_t<T, LAW_SVK, VEC>(a, fuse, grid, st);
+    case LAW_NH: return launch_step_t<T, LAW_NH, VEC>(a, fuse, grid, st);
+    default: return launch_step_t<T, LAW_LOGNH, VEC>(a, fuse, grid, st);
     }
 }
 
-cudaError_t launch_step(int storage_bytes, int law, const void *args, int grid, cudaStream_t st)
+cudaError_t launch_step(int storage_bytes, int law, bool fuse, const void *args, int grid, cudaStream_t st)
 {
-    if (storage_bytes == 8) return launch_step_law<double>(law, *static_cast<const StepArgs<double> *>(args), grid, st);
-    return launch_step_law<float>(law, *static_cast<const StepArgs<float> *>(args), grid, st);
+    if (storage_bytes == 8)
+        return launch_step_law<double>(law, *static_cast<const StepArgs<double> *>(args), fuse, grid, st);
+    return launch_step_law<float>(law, *static_cast<const StepArgs<float> *>(args), fuse, grid, st);
 }
 
 cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st)
@@ -397,16 +582,35 @@ cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStr
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_ghosts_t(const EdgeArgs &a, int grid, cudaStream_t st)
+{
+    switch (a.m.law) {
+    case LAW_SVK: k_ghosts<T, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
+    case LAW_NH: k_ghosts<T, LAW_NH><<<grid, 128, 0, st>>>(a); break;
+    default: k_ghosts<T, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghosts(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+    return storage_bytes == 8 ? launch_ghosts_t<double>(a, grid, st) : launch_ghosts_t<float>(a, grid, st);
+}
+
 int step_blocks_per_sm(int storage_bytes, int law)
 {
     int n = 0;
     const void *fn;
     if (storage_bytes == 8)
-        fn = (law == LAW_SVK) ? (const void *)k_step<double, LAW_SVK, 2>
-             : (law == LAW_NH) ? (const void *)k_step<double, LAW_NH, 2> : (const void *)k_step<double, LAW_LOGNH, 2>;
+        fn = (law == LAW_SVK) ? (const void *)k_step<double, LAW_SVK, 2, true>
+             : (law == LAW_NH) ? (const void *)k_step<double, LAW_NH, 2, true>
+                               : (const void *)k_step<double, LAW_LOGNH, 2, true>;
     else
-        fn = (law == LAW_SVK) ? (const void *)k_step<float, LAW_SVK, 4>
-             : (law == LAW_NH) ? (const void *)k_step<float, LAW_NH, 4> : (const void *)k_step<float, LAW_LOGNH, 4>;
+        fn = (law == LAW_SVK) ? (const void *)k_step<float, LAW_SVK, 4, true>
+             : (law == LAW_NH) ? (const void *)k_step<float, LAW_NH, 4, true>
+                               : (const void *)k_step<float, LAW_LOGNH, 4, true>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
     return n;
 }

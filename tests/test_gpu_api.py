@@ -200,13 +200,21 @@ def test_checkpoint_roundtrip_is_exact(lbm, storage):
     L.close()
 
 
-def test_profile_counts_launches(lbm):
-    L = make(lbm, 300, 200)
+@pytest.mark.parametrize("fb_mode", [0, 1])
+def test_profile_counts_launches(lbm, fb_mode):
+    """Node form: the step kernel writes the next step's ghost cells, so the
+    ghost kernel runs once after initialization and again only after new edge
+    data. Extrapolated form: the edge kernel runs before every step."""
+    L = make(lbm, 300, 200, fb_mode=fb_mode)
+    lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.01, 0.0))
     lbm.lbm_init(L.ctx, rest(300, 200))
     lbm.lbm_profile(L.ctx, True)
     lbm.lbm_step(L.ctx, 7)
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.0))
+    lbm.lbm_step(L.ctx, 5)
     p = lbm.lbm_profile_read(L.ctx)
-    assert p["step"][0] == 7 and p["edges"][0] == 7
+    assert p["step"][0] == 12 and p["edges"][0] == (2 if fb_mode == 0 else 12)
     assert p["step"][1] > 0 and p["edges"][1] > 0
     lbm.lbm_profile(L.ctx, False)
     assert lbm.lbm_bytes_per_node_update(L.ctx) == 224.0
