@@ -16,7 +16,8 @@ Reported (one JSON line on rank 0):
   roofline  the bulk kernel's algorithmic bytes per launch (224 B per node)
             over its mean event-timed launch duration, against the measured
             HBM copy bandwidth;
-  forms     the same step stored in FP64 and the 8192^2 periodic workload;
+  forms     the same step with FP64, BF16 and FP16 population storage, and the
+            8192^2 periodic workload in FP32 and BF16;
   cpu_baseline  the FP64 CPU oracle on a bounded sample (512 x 256 scaled
             specimen) on one host core.
 --impl reference times the oracle alone as the reference arm.
@@ -258,19 +259,32 @@ def run_ours(args, rank, ws, dist):
             "value": N * k / (ms64 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
             "kernel_GBs": b64 * N / (t64 / max(n64, 1) * 1e-3) / 1e9, "bytes_per_node": b64,
             "note": "FP64 populations (parity mode); FP64 ALU-bound on GB300"}
+        for name, st in (("bf16", lbm.LBM_STORE_BF16), ("f16", lbm.LBM_STORE_F16)):
+            L = setup_ctx(lbm, w, st, U0, u0)
+            msh, profh = timed_steps(lbm, torch, L, k, 5, None)
+            bh = lbm.lbm_bytes_per_node_update(L.ctx)
+            L.close()
+            nh, th = profh["step"]
+            gbs = bh * N / (th / max(nh, 1) * 1e-3) / 1e9
+            forms[name + "_clamped_specimen_4096x2048"] = {
+                "value": N * k / (msh * 1e-3) / 1e6, "unit": UNIT, "steps": k, "kernel_GBs": gbs,
+                "roofline_frac": gbs / peak, "bytes_per_node": bh,
+                "note": "populations stored as %s offsets from the rest equilibrium, FP32 compute, FP64 u*" % name}
         wp = fourier_periodic()
         Up, up = wp.fields()
-        L = setup_ctx(lbm, wp, lbm.LBM_STORE_F32, Up, up)
+        for name, st in (("fp32", lbm.LBM_STORE_F32), ("bf16", lbm.LBM_STORE_BF16)):
+            L = setup_ctx(lbm, wp, st, Up, up)
+            ms8, prof8 = timed_steps(lbm, torch, L, k, 5, None)
+            b8 = lbm.lbm_bytes_per_node_update(L.ctx)
+            L.close()
+            n8, t8 = prof8["step"]
+            N8 = wp.nx * wp.ny
+            gbs = b8 * N8 / (t8 / max(n8, 1) * 1e-3) / 1e9
+            forms[name + "_periodic_8192x8192"] = {
+                "value": N8 * k / (ms8 * 1e-3) / 1e6, "unit": UNIT, "steps": k, "kernel_GBs": gbs,
+                "roofline_frac": gbs / peak, "bytes_per_node": b8,
+                "note": "16-mode random velocity field, NH lambda=1.5 mu=0.75, omega=2"}
         del Up, up
-        ms8, prof8 = timed_steps(lbm, torch, L, k, 5, None)
-        L.close()
-        n8, t8 = prof8["step"]
-        N8 = wp.nx * wp.ny
-        forms["fp32_periodic_8192x8192"] = {
-            "value": N8 * k / (ms8 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
-            "kernel_GBs": bpn * N8 / (t8 / max(n8, 1) * 1e-3) / 1e9,
-            "roofline_frac": bpn * N8 / (t8 / max(n8, 1) * 1e-3) / 1e9 / peak,
-            "note": "16-mode random velocity field, NH lambda=1.5 mu=0.75, omega=2"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

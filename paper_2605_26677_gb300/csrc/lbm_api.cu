@@ -23,7 +23,6 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     double *ustar = nullptr;
     int *d_status = nullptr;
-    long long *d_step = nullptr; // [2]: steps completed, one slot per buffer parity
     double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
     double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
     int cur = 0;
@@ -115,8 +114,6 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.fout = static_cast<T *>(c->f[cur ^ 1]);
     a.ustar = c->ustar;
     a.status = c->d_status;
-    a.step_in = c->d_step + cur;
-    a.step_out = c->d_step + (cur ^ 1);
     a.L = c->L;
     const double w = c->cfg.omega;
     a.omega = (T)w;
@@ -131,12 +128,14 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.mu = (T)c->m.mu;
     a.c = (T)c->cfg.c;
     a.dt = c->dt;
+    // this launch computes f*^{n+1} (n = c->step) and writes the ghosts the
+    // next step pulls, whose edge data belong to t^{n+1} + dt/2 (Eq. 23)
+    const double th = ((double)c->step + 1.5) * c->dt;
     for (int e = 0; e < 4; ++e) {
         a.kind[e] = c->edge[e].kind;
-        a.timefn[e] = c->edge[e].timefn;
         a.value[e][0] = c->edge[e].value[0];
         a.value[e][1] = c->edge[e].value[1];
-        for (int i = 0; i < 4; ++i) a.tp[e][i] = c->edge[e].tp[i];
+        a.g[e] = timefn(c->edge[e].timefn, c->edge[e].tp, th);
         a.profile[e] = c->edge[e].profile;
     }
     return a;
@@ -160,7 +159,9 @@ EdgeArgs edge_args(const lbm_ctx *c, int cur)
     a.fb_mode = c->cfg.fb_mode;
     a.xper = xper(c);
     a.yper = yper(c);
-    a.step = c->d_step + cur;
+    // the ghosts of the stored f*^n serve the pull of step n + 1: t^n + dt/2
+    const double th = ((double)c->step + 0.5) * c->dt;
+    for (int e = 0; e < 4; ++e) a.g[e] = timefn(c->edge[e].timefn, c->edge[e].tp, th);
     a.status = c->d_status;
     return a;
 }
@@ -196,15 +197,15 @@ lbm_status do_step(lbm_ctx *c, int64_t nsteps)
             const EdgeArgs ea = edge_args(c, c->cur);
             if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
             if (fuse)
-                CK(c, launch_ghosts(c->eb, ea, c->edge_blk_end[3], c->st));
+                CK(c, launch_ghosts(c->cfg.storage, ea, c->edge_blk_end[3], c->st));
             else
-                CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
+                CK(c, launch_edges(c->cfg.storage, ea, c->edge_blk_end[3], c->st));
             if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
             c->ghosts_dirty = false;
         }
         const StepArgs<T> sa = step_args<T>(c, c->cur);
         if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
-        CK(c, launch_step(c->eb, c->m.law, fuse, &sa, c->grid_step, c->st));
+        CK(c, launch_step(c->cfg.storage, c->m.law, fuse, &sa, c->grid_step, c->st));
         if (prof && record(c, c->ev_step) != LBM_OK) return LBM_ERR_CUDA;
         c->cur ^= 1;
         c->step += 1;
@@ -226,7 +227,7 @@ lbm_status read_device(lbm_ctx *c, double *U, double *P, double *sigma, double *
     a.P = P;
     a.sigma = sigma;
     a.u = u;
-    CK(c, launch_read(c->eb, a, c->st));
+    CK(c, launch_read(c->cfg.storage, a, c->st));
     return LBM_OK;
 }
 
@@ -256,7 +257,7 @@ lbm_status check_ready(lbm_ctx *c)
 
 struct SaveHeader {
     char magic[8];
-    int32_t version, nx, ny, eb;
+    int32_t version, nx, ny, storage;
     int64_t step;
 };
 
@@ -303,9 +304,9 @@ lbm_status refresh_ghosts(lbm_ctx *c)
 {
     const EdgeArgs ea = edge_args(c, c->cur);
     if (c->cfg.fb_mode == LBM_FB_NODE)
-        CK(c, launch_ghosts(c->eb, ea, c->edge_blk_end[3], c->st));
+        CK(c, launch_ghosts(c->cfg.storage, ea, c->edge_blk_end[3], c->st));
     else
-        CK(c, launch_edges(c->eb, ea, c->edge_blk_end[3], c->st));
+        CK(c, launch_edges(c->cfg.storage, ea, c->edge_blk_end[3], c->st));
     c->ghosts_dirty = false;
     return LBM_OK;
 }
@@ -323,20 +324,19 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     if (!cfg) return fail(nullptr, LBM_ERR_ARG, "cfg is NULL");
     if (cfg->nx < 1 || cfg->ny < 1) return fail(nullptr, LBM_ERR_ARG, "nx and ny must be >= 1 (empty lattice)");
     if (cfg->nx > (1 << 24) || cfg->ny > (1 << 24)) return fail(nullptr, LBM_ERR_ARG, "nx or ny above 2^24");
+    // the step kernels index (row, 64-node segment) tasks with 32-bit integers
+    if ((long long)cfg->ny * ((cfg->nx + 63) / 64) >= (1LL << 31)) return fail(nullptr, LBM_ERR_ARG, "grid too large");
     if (!(cfg->dx > 0.0) || !is_finite(cfg->dx)) return fail(nullptr, LBM_ERR_ARG, "dx must be finite and > 0");
     if (!(cfg->c > 0.0) || !is_finite(cfg->c)) return fail(nullptr, LBM_ERR_ARG, "c must be finite and > 0");
     if (!(cfg->omega > 0.0) || !(cfg->omega <= 2.0)) return fail(nullptr, LBM_ERR_ARG, "omega must be in (0, 2]");
-    if (cfg->storage == LBM_STORE_BF16 || cfg->storage == LBM_STORE_F16)
-        return fail(nullptr, LBM_ERR_UNSUPPORTED, "BF16/FP16 offset storage is not built in this version");
-    if (cfg->storage != LBM_STORE_F64 && cfg->storage != LBM_STORE_F32)
-        return fail(nullptr, LBM_ERR_ARG, "unknown storage");
+    if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_F16) return fail(nullptr, LBM_ERR_ARG, "unknown storage");
     if (cfg->fb_mode != LBM_FB_NODE && cfg->fb_mode != LBM_FB_EXTRAP2) return fail(nullptr, LBM_ERR_ARG, "unknown fb_mode");
 
     lbm_ctx *c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
     c->cfg = *cfg;
     c->st = static_cast<cudaStream_t>(cfg->stream);
-    c->eb = (cfg->storage == LBM_STORE_F64) ? 8 : 4;
+    c->eb = (cfg->storage == LBM_STORE_F64) ? 8 : (cfg->storage == LBM_STORE_F32) ? 4 : 2;
     c->dt = cfg->dx / cfg->c;
     const int line = 128 / c->eb, vec = 16 / c->eb;
     c->L.nx = cfg->nx;
@@ -377,13 +377,11 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     CKC(cudaMalloc(&c->f[1], fbytes));
     CKC(cudaMalloc((void **)&c->ustar, ubytes));
     CKC(cudaMalloc((void **)&c->d_status, sizeof(int)));
-    CKC(cudaMalloc((void **)&c->d_step, 2 * sizeof(long long)));
     CKC(cudaMalloc((void **)&c->d_diag, (size_t)(diag_blocks(c->L) * 10 + 10) * sizeof(double)));
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->ustar, 0, ubytes, c->st));
     CKC(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
-    CKC(cudaMemsetAsync(c->d_step, 0, 2 * sizeof(long long), c->st));
     CKC(cudaStreamSynchronize(c->st));
 #undef CKC
     int sms = 0;
@@ -403,7 +401,6 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->f[1]);
     cudaFree(c->ustar);
     cudaFree(c->d_status);
-    cudaFree(c->d_step);
     cudaFree(c->d_diag);
     for (int e = 0; e < 4; ++e) cudaFree(c->d_profile[e]);
     delete c;
@@ -429,8 +426,8 @@ lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32
     CK(c, cudaSetDevice(c->cfg.device));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
-    const int per_sm = step_blocks_per_sm(c->eb, c->m.law);
-    const int vec = step_vec(c->eb);
+    const int per_sm = step_blocks_per_sm(c->cfg.storage, c->m.law);
+    const int vec = step_vec(c->cfg.storage);
     const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
     const long long needed = (tasks + 3) / 4; // 4 warps per block
     long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
@@ -507,8 +504,7 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     a.xper = xper(c);
     a.yper = yper(c);
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
-    CK(c, cudaMemsetAsync(c->d_step, 0, 2 * sizeof(long long), c->st));
-    CK(c, launch_init(c->eb, a, c->st));
+    CK(c, launch_init(c->cfg.storage, a, c->st));
     c->cur = 0;
     c->step = 0;
     c->initialized = true;
@@ -650,7 +646,7 @@ lbm_status lbm_diagnostics(lbm_ctx *c, double out[10])
     a.b2 = c->b[1];
     a.partial = c->d_diag;
     a.out = c->d_diag + (size_t)diag_blocks(c->L) * 10;
-    CK(c, launch_diag(c->eb, a, c->st));
+    CK(c, launch_diag(c->cfg.storage, a, c->st));
     CK(c, cudaMemcpyAsync(out, a.out, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     return sync_status(c);
 }
@@ -676,7 +672,7 @@ lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
     h.version = 2;
     h.nx = c->L.nx;
     h.ny = c->L.ny;
-    h.eb = c->eb;
+    h.storage = c->cfg.storage;
     h.step = c->step;
     std::memcpy(buf, &h, sizeof h);
     char *p = static_cast<char *>(buf) + sizeof h;
@@ -708,7 +704,7 @@ lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
     std::memcpy(&h, buf, sizeof h);
     const size_t N = (size_t)c->L.nx * c->L.ny;
     if (std::memcmp(h.magic, "TLVLBM02", 8) != 0 || h.version != 2) return fail(c, LBM_ERR_ARG, "not a checkpoint");
-    if (h.nx != c->L.nx || h.ny != c->L.ny || h.eb != c->eb)
+    if (h.nx != c->L.nx || h.ny != c->L.ny || h.storage != c->cfg.storage)
         return fail(c, LBM_ERR_ARG, "checkpoint grid or storage differs from the context");
     if (bytes < sizeof h + 24 * N * c->eb + 2 * N * sizeof(double) + ghost_elems(c) * c->eb)
         return fail(c, LBM_ERR_ARG, "truncated checkpoint");
@@ -731,8 +727,6 @@ lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
     if (s != LBM_OK) return s;
     c->step = h.step;
     c->ghosts_dirty = false;
-    const long long st[2] = {h.step, h.step};
-    CK(c, cudaMemcpyAsync(c->d_step, st, sizeof st, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
     return sync_status(c);
 }

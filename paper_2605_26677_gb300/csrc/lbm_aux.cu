@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
             for (int k = 0; k < 6; ++k) {
                 double fs = f[q][k] + a.omega * (feq[q][k] - f[q][k]) + (k < 2 ? src[k] : 0.0);
                 if (k == 2 || k == 5) fs -= 0.25; // store the offset from f_rest
-                fout[pidx(a.L, q, k, x, y)] = (T)fs;
+                fout[pidx(a.L, q, k, x, y)] = to_store<T>(fs);
             }
         for (int k = 0; k < 2; ++k) {
             const double u0 = a.u0 ? a.u0[k * N + n] : 0.0;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) k_read(const ReadArgs a)
         double S[6];
         for (int k = 0; k < 6; ++k) {
             double s = 0.0;
-            for (int q = 0; q < 4; ++q) s += (double)f[pidx(a.L, q, k, x, y)];
+            for (int q = 0; q < 4; ++q) s += (double)ld_r(f[pidx(a.L, q, k, x, y)]);
             S[k] = s;
         }
         const double v1 = S[0] - 0.5 * a.dt * a.b1, v2 = S[1] - 0.5 * a.dt * a.b2;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const DiagArgs a)
         double S[6];
         for (int k = 0; k < 6; ++k) {
             double s = 0.0;
-            for (int q = 0; q < 4; ++q) s += (double)f[pidx(a.L, q, k, x, y)];
+            for (int q = 0; q < 4; ++q) s += (double)ld_r(f[pidx(a.L, q, k, x, y)]);
             S[k] = s;
         }
         const double v1 = S[0] - 0.5 * a.dt * a.b1, v2 = S[1] - 0.5 * a.dt * a.b2;
@@ -301,24 +301,22 @@ static int grid_for(long long n, int threads)
     return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_init(int storage_bytes, const InitArgs &a, cudaStream_t st)
+cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st)
 {
     const int g = grid_for((long long)a.L.nx * a.L.ny, 128);
-    if (storage_bytes == 8)
-        k_init<double><<<g, 128, 0, st>>>(a);
-    else
-        k_init<float><<<g, 128, 0, st>>>(a);
-    return cudaGetLastError();
+    return with_storage(storage, [&](auto tag) {
+        k_init<decltype(tag)><<<g, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_read(int storage_bytes, const ReadArgs &a, cudaStream_t st)
+cudaError_t launch_read(int storage, const ReadArgs &a, cudaStream_t st)
 {
     const int g = grid_for((long long)a.L.nx * a.L.ny, 128);
-    if (storage_bytes == 8)
-        k_read<double><<<g, 128, 0, st>>>(a);
-    else
-        k_read<float><<<g, 128, 0, st>>>(a);
-    return cudaGetLastError();
+    return with_storage(storage, [&](auto tag) {
+        k_read<decltype(tag)><<<g, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
 int diag_blocks(const Layout &L)
@@ -329,13 +327,13 @@ int diag_blocks(const Layout &L)
     return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_diag(int storage_bytes, const DiagArgs &a, cudaStream_t st)
+cudaError_t launch_diag(int storage, const DiagArgs &a, cudaStream_t st)
 {
     const int nb = diag_blocks(a.L);
-    if (storage_bytes == 8)
-        k_diag_partial<double><<<nb, DIAG_THREADS, 0, st>>>(a);
-    else
-        k_diag_partial<float><<<nb, DIAG_THREADS, 0, st>>>(a);
+    with_storage(storage, [&](auto tag) {
+        k_diag_partial<decltype(tag)><<<nb, DIAG_THREADS, 0, st>>>(a);
+        return 0;
+    });
     k_diag_final<<<1, DIAG_THREADS, 0, st>>>(a, nb);
     return cudaGetLastError();
 }

@@ -16,9 +16,63 @@
 // over q of the F-components gives G = F - I directly.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace tlv {
+
+// ---------------------------------------------------------------- storage
+// Populations are stored as S (double, float, __half or __nv_bfloat16) and
+// computed in Prec<S>::R: double for double storage, float otherwise.
+enum { STORE_F64 = 0, STORE_F32 = 1, STORE_BF16 = 2, STORE_F16 = 3 };
+
+template <typename S>
+struct Prec {
+    using R = float;
+};
+template <>
+struct Prec<double> {
+    using R = double;
+};
+
+__device__ __forceinline__ double ld_r(double v) { return v; }
+__device__ __forceinline__ float ld_r(float v) { return v; }
+__device__ __forceinline__ float ld_r(__half v) { return __half2float(v); }
+__device__ __forceinline__ float ld_r(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// round to the storage type (nearest even)
+template <typename S>
+__device__ __forceinline__ S to_store(double v);
+template <>
+__device__ __forceinline__ double to_store<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_store<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __half to_store<__half>(double v) { return __double2half(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <typename S>
+__device__ __forceinline__ S to_store(float v);
+template <>
+__device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Call fn with a value of the storage type selected by `storage`.
+template <typename Fn>
+__host__ auto with_storage(int storage, Fn fn)
+{
+    switch (storage) {
+    case STORE_F64: return fn(double(0));
+    case STORE_BF16: return fn(__nv_bfloat16());
+    case STORE_F16: return fn(__half());
+    default: return fn(float(0));
+    }
+}
 
 enum { EDGE_LEFT = 0, EDGE_RIGHT = 1, EDGE_BOTTOM = 2, EDGE_TOP = 3 };
 enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_TRACTION = 2 };
@@ -48,23 +102,23 @@ struct EdgeDesc {
     const double *profile; // device, one factor per edge node, or nullptr
 };
 
+// T is the compute type; the populations are stored as the kernel's S
 template <typename T>
 struct StepArgs {
-    const T *__restrict__ fin;   // post-collision populations f*^{n-1}, ghosts filled
-    T *__restrict__ fout;        // post-collision populations f*^n
+    const void *fin;             // post-collision populations f*^{n-1}, ghosts filled
+    void *fout;                  // post-collision populations f*^n
     double *__restrict__ ustar;  // u*, advanced by dt v^n
     int *status;                 // latched ST_* bits
-    const long long *step_in;    // steps completed before this launch (n - 1)
-    long long *step_out;         // receives n (the other slot of a ping-pong pair)
     Layout L;
     T omega, one_m_omega, inv2c, quarter;
     T hdtb1, hdtb2;              // (dt/2) b
     T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
     T lam, mu, c;
     double dt;
-    // edge rules, used when the kernel also writes the ghost cells of fout
-    int kind[4], timefn[4];
-    double value[4][2], tp[4][4];
+    // edge rules, used when the kernel also writes the ghost cells of fout:
+    // value * g * profile[s], g = g(t^n + dt/2) evaluated once on the host
+    int kind[4];
+    double value[4][2], g[4];
     const double *profile[4];
 };
 
@@ -76,7 +130,7 @@ struct EdgeArgs {
     Material m;
     double c, dt, dx, hdtb1, hdtb2;
     int fb_mode, xper, yper;
-    const long long *step;
+    double g[4];              // time factor of each edge's data for the coming pull
     int *status;
 };
 
@@ -183,8 +237,9 @@ __device__ __forceinline__ void tangent_jvp(int law, const double F[4], const do
     for (int m = 0; m < 4; ++m) dP[m] = mu * dF[m] + a * HdF * H[m] + b * M[m];
 }
 
-// Boundary-data time function g(t) (shapes of Eqs. 33, 35 and Sec. 5.4).
-__device__ __forceinline__ double timefn(int kind, const double *tp, double t)
+// Boundary-data time function g(t) (shapes of Eqs. 33, 35 and Sec. 5.4),
+// evaluated on the host once per step and edge.
+__host__ __device__ inline double timefn(int kind, const double *tp, double t)
 {
     const double pi = 3.14159265358979323846;
     switch (kind) {

@@ -171,12 +171,12 @@ __device__ __forceinline__ void edge_ghost(int e, int kind, const R fo[6], const
     }
 }
 
-// edge data at t for position s of edge E
-__device__ __forceinline__ void edge_value(const EdgeDesc &E, int s, double t, double val[2])
+// edge data for position s of edge E with time factor g
+__device__ __forceinline__ void edge_value(const EdgeDesc &E, int s, double g, double val[2])
 {
-    const double g = timefn(E.timefn, E.tp, t) * (E.profile ? E.profile[s] : 1.0);
-    val[0] = E.value[0] * g;
-    val[1] = E.value[1] * g;
+    const double f = g * (E.profile ? E.profile[s] : 1.0);
+    val[0] = E.value[0] * f;
+    val[1] = E.value[1] * f;
 }
 
 } // namespace tlv

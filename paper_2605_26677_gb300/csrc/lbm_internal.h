@@ -11,13 +11,14 @@ namespace tlv {
 
 // lbm_step.cu
 // fuse: the step kernel also writes the next step's ghost cells (node form)
-cudaError_t launch_step(int storage_bytes, int law, bool fuse, const void *step_args, int grid, cudaStream_t st);
+// storage: STORE_F64 / F32 / BF16 / F16
+cudaError_t launch_step(int storage, int law, bool fuse, const void *step_args, int grid, cudaStream_t st);
 // ghost cells of the current buffer: k_edges (either F^b form, FP64 Newton)
 // and k_ghosts (node form, the fused kernel's arithmetic)
-cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st);
-cudaError_t launch_ghosts(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st);
-int step_blocks_per_sm(int storage_bytes, int law);
-int step_vec(int storage_bytes);
+cudaError_t launch_edges(int storage, const EdgeArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_ghosts(int storage, const EdgeArgs &a, int grid, cudaStream_t st);
+int step_blocks_per_sm(int storage, int law);
+int step_vec(int storage);
 
 // lbm_aux.cu
 struct InitArgs {
@@ -31,7 +32,7 @@ struct InitArgs {
     double c, dt, dx, omega, b1, b2;
     int order, xper, yper;
 };
-cudaError_t launch_init(int storage_bytes, const InitArgs &a, cudaStream_t st);
+cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st);
 
 struct ReadArgs {
     const void *f;      // current post-collision populations
@@ -44,7 +45,7 @@ struct ReadArgs {
     double *sigma;      // 4 x N or nullptr
     double *u;          // 2 x N or nullptr
 };
-cudaError_t launch_read(int storage_bytes, const ReadArgs &a, cudaStream_t st);
+cudaError_t launch_read(int storage, const ReadArgs &a, cudaStream_t st);
 
 struct DiagArgs {
     const void *f;
@@ -55,7 +56,7 @@ struct DiagArgs {
     double *out;        // [10]
 };
 int diag_blocks(const Layout &L);
-cudaError_t launch_diag(int storage_bytes, const DiagArgs &a, cudaStream_t st);
+cudaError_t launch_diag(int storage, const DiagArgs &a, cudaStream_t st);
 
 // lbm_api.cu: message returned by lbm_last_error(NULL) on this host thread
 void set_thread_error(const std::string &msg);

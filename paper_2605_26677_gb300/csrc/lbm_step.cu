@@ -24,6 +24,11 @@ struct alignas(sizeof(T) * N) Pack {
 
 #define FULL_MASK 0xffffffffu
 
+// nodes per lane of the 16-bit storage kernel
+#ifndef STEP16_V
+#define STEP16_V 4
+#endif
+
 // ---------------------------------------------------------------- bulk step
 // A warp owns VEC*32 consecutive nodes of one row (lane l: nodes x0..x0+VEC-1,
 // x0 = seg*32*VEC + l*VEC) and loops over (row, segment) tasks. The +y and -y
@@ -49,35 +54,143 @@ __device__ __forceinline__ void state_from_fstar(const T f0[6], const T f1[6], c
     U[1] -= hb2;
 }
 
-template <typename T, int LAW, int VEC, bool FUSE>
-__global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
+// One node: Eq. (10) state recovery, P(F) (Appendix A), Eq. (7) fluxes,
+// Eq. (12) equilibrium and Eq. (14) collision, in place on the four streamed
+// populations f[q][k] (offsets). Returns the velocity v^n.
+template <int LAW, typename T>
+__device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, bool real, unsigned &flags, T &v1,
+                                             T &v2)
 {
-    using PK = Pack<T, VEC>;
+    T U[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U[k] = (f[0][k] + f[2][k]) + (f[1][k] + f[3][k]);
+    U[0] += a.hdtb1;
+    U[1] += a.hdtb2;
+    T P11, P12, P21, P22, dJ;
+    piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], a.lam, a.mu, P11, P12, P21, P22, dJ);
+    if (real) {
+        if (!(dJ > T(-1))) flags |= ST_BAD_J;
+        if (!(fabs(U[0]) + fabs(U[1]) + fabs(dJ) < T(INFINITY))) flags |= ST_NONFINITE;
+    }
+    v1 = U[0];
+    v2 = U[1];
+    // f^eq_q = U/4 + (1/2c)(i Phi_X + j Phi_Y)
+    const T PhiX[6] = {-P11, -P21, -U[0], T(0), -U[1], T(0)};
+    const T PhiY[6] = {-P12, -P22, T(0), -U[0], T(0), -U[1]};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const T qU = a.quarter * U[k];
+        const T fx = a.inv2c * PhiX[k], fy = a.inv2c * PhiY[k];
+        const T src = (k == 0) ? a.src1 : (k == 1) ? a.src2 : T(0);
+        // f* = (1 - omega) f + omega f^eq + dt (2 - omega) w B
+        f[0][k] = a.one_m_omega * f[0][k] + a.omega * (qU + fx) + src;
+        f[2][k] = a.one_m_omega * f[2][k] + a.omega * (qU - fx) + src;
+        f[1][k] = a.one_m_omega * f[1][k] + a.omega * (qU + fy) + src;
+        f[3][k] = a.one_m_omega * f[3][k] + a.omega * (qU - fy) + src;
+    }
+}
+
+// Ghost cells that node (x, y) is responsible for, from its post-collision
+// populations f (compute type). Bottom ghost row (plane 1, y = -1), top ghost
+// row (plane 3, y = ny), left ghost column (plane 0, x = -1), right ghost
+// column (plane 2, x = nx), with the edge data of the step that will pull
+// these values.
+template <int LAW, typename S, typename T>
+__device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, S *fout,
+                                            unsigned &flags)
+{
+    const int nx = a.L.nx, ny = a.L.ny;
+    auto put = [&](int e, int gx, int gy, const T val[6]) {
+        const int q = edge_dmiss(e);
+        S *dst = fout + (long long)(q * 6) * a.L.plane + (long long)(gy + 1) * a.L.pitch + a.L.xoff + gx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[k * a.L.plane] = to_store<S>(val[k]);
+    };
+    auto rule = [&](int e, int s, int gx, int gy) {
+        T U[6], out[6];
+        state_from_fstar(f[0], f[1], f[2], f[3], a.hdtb1, a.hdtb2, U);
+        const double g = a.g[e] * (a.profile[e] ? a.profile[e][s] : 1.0);
+        const double val[2] = {a.value[e][0] * g, a.value[e][1] * g};
+        edge_ghost<LAW, T>(e, a.kind[e], f[edge_dout(e)], U, val, a.c, a.lam, a.mu, out, flags);
+        put(e, gx, gy, out);
+    };
+    if (a.kind[EDGE_BOTTOM] == BC_PERIODIC) {
+        if (y == ny - 1) put(EDGE_BOTTOM, x, -1, f[1]);
+        if (y == 0) put(EDGE_TOP, x, ny, f[3]);
+    } else {
+        if (y == 0) rule(EDGE_BOTTOM, x, x, -1);
+        if (y == ny - 1) rule(EDGE_TOP, x, x, ny);
+    }
+    if (a.kind[EDGE_LEFT] == BC_PERIODIC) {
+        if (x == nx - 1) put(EDGE_LEFT, -1, y, f[0]);
+        if (x == 0) put(EDGE_RIGHT, nx, y, f[2]);
+    } else {
+        if (x == 0) rule(EDGE_LEFT, y, -1, y);
+        if (x == nx - 1) rule(EDGE_RIGHT, y, nx, y);
+    }
+}
+
+// Task order shared by both step kernels: (row, segment) with the segments of
+// row y rotated by y -- with a warp count that is a multiple of the number of
+// segments, an unrotated order would give every edge segment (and its Newton
+// solves) to the same few warps.
+__device__ __forceinline__ void task_coords(int task, int nseg, int &y, int &seg)
+{
+    y = task / nseg;
+    seg = (task - y * nseg + y) % nseg;
+}
+
+// After a lane has stored its nodes, the ghost cells its boundary nodes are
+// responsible for are written from the stored post-collision values (read
+// back by the same thread), so the edge work never adds to the register peak
+// of the streaming loop, and it sees exactly the values the ghost-refresh
+// kernel would read.
+template <int LAW, typename S, int VEC>
+__device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> &a, S *fout, long long row, int x0,
+                                            int y, unsigned &flags)
+{
+    using T = typename Prec<S>::R;
+    const int nx = a.L.nx, ny = a.L.ny;
+    const bool edge_row = (y == 0 || y == ny - 1);
+    if (!edge_row && x0 != 0 && !(x0 <= nx - 1 && nx - 1 < x0 + VEC)) return;
+#pragma unroll 1
+    for (int e = 0; e < VEC; ++e) {
+        const int x = x0 + e;
+        if (x >= nx) break;
+        if (!edge_row && x != 0 && x != nx - 1) continue;
+        T fq[4][6];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(fout[(q * 6 + k) * a.L.plane + row + e]);
+        node_ghosts<LAW, S, T>(fq, x, y, a, fout, flags);
+    }
+}
+
+// FP64 and FP32 storage: VEC nodes per lane as 16-byte vectors, unpacked.
+template <typename S, int LAW, int VEC, bool FUSE>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
+{
+    using T = typename Prec<S>::R;  // compute type
+    using PK = Pack<S, VEC>;        // stored vector
     using PD = Pack<double, VEC>;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
-    const long long nw = (long long)gridDim.x * wpb;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int nw = gridDim.x * wpb;
     const int nx = a.L.nx, ny = a.L.ny;
     const int segw = 32 * VEC;
     const int nseg = (nx + segw - 1) / segw;
-    const long long ntask = (long long)ny * nseg;
+    const int ntask = ny * nseg;  // < 2^31 for every grid the library accepts
     const long long plane = a.L.plane;
     const int pitch = a.L.pitch;
-    const T *__restrict__ fin = a.fin;
-    T *__restrict__ fout = a.fout;
-    const long long n_in = *a.step_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.step_out = n_in + 1;
-    // edge data for the next step's pull is sampled at t^{n} + dt/2 (Eq. 23)
-    const double th = ((double)n_in + 1.5) * a.dt;
+    const S *__restrict__ fin = static_cast<const S *>(a.fin);
+    S *__restrict__ fout = static_cast<S *>(a.fout);
 
     unsigned flags = 0;
-    for (long long task = gw; task < ntask; task += nw) {
-        const int y = (int)(task / nseg);
-        // the segments of row y are taken in an order rotated by y: with a warp
-        // count that is a multiple of nseg, an unrotated order would give every
-        // edge segment (and its Newton solves) to the same few warps
-        const int seg = (int)((task - (long long)y * nseg + y) % nseg);
+    for (int task = gw; task < ntask; task += nw) {
+        int y, seg;
+        task_coords(task, nseg, y, seg);
         const int x0 = seg * segw + lane * VEC;
         const bool act = x0 < nx;   // lane owns at least one real node
         const bool ld0 = x0 <= nx;  // lane's vector holds a real node or the right ghost column
@@ -95,50 +208,31 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
                 c1 = *reinterpret_cast<const PK *>(fin + (1 * 6 + k) * plane + row - pitch);
                 c3 = *reinterpret_cast<const PK *>(fin + (3 * 6 + k) * plane + row + pitch);
             }
-            T left = __shfl_up_sync(FULL_MASK, c0.v[VEC - 1], 1);
-            T right = __shfl_down_sync(FULL_MASK, c2.v[0], 1);
-            if (act && lane == 0) left = fin[(0 * 6 + k) * plane + row - 1];
-            if (act && lane == 31) right = fin[(2 * 6 + k) * plane + row + VEC];
+            T left = __shfl_up_sync(FULL_MASK, ld_r(c0.v[VEC - 1]), 1);
+            T right = __shfl_down_sync(FULL_MASK, ld_r(c2.v[0]), 1);
+            if (act && lane == 0) left = ld_r(fin[(0 * 6 + k) * plane + row - 1]);
+            if (act && lane == 31) right = ld_r(fin[(2 * 6 + k) * plane + row + VEC]);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                f[0][k][e] = (e == 0) ? left : c0.v[e - 1];          // from x - 1 (Eq. 15)
-                f[2][k][e] = (e == VEC - 1) ? right : c2.v[e + 1];   // from x + 1
-                f[1][k][e] = c1.v[e];                                // from y - 1
-                f[3][k][e] = c3.v[e];                                // from y + 1
+                f[0][k][e] = (e == 0) ? left : ld_r(c0.v[e - 1]);          // from x - 1 (Eq. 15)
+                f[2][k][e] = (e == VEC - 1) ? right : ld_r(c2.v[e + 1]);   // from x + 1
+                f[1][k][e] = ld_r(c1.v[e]);                                // from y - 1
+                f[3][k][e] = ld_r(c3.v[e]);                                // from y + 1
             }
         }
-
         T vel[2][VEC];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            // Eq. (10): U = sum_q f_q + (dt/2) B (offsets: F-components give G = F - I)
-            T U[6];
+            T fq[4][6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) U[k] = (f[0][k][e] + f[2][k][e]) + (f[1][k][e] + f[3][k][e]);
-            U[0] += a.hdtb1;
-            U[1] += a.hdtb2;
-            T P11, P12, P21, P22, dJ;
-            piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], a.lam, a.mu, P11, P12, P21, P22, dJ);
-            if (x0 + e < nx) {
-                if (!(dJ > T(-1))) flags |= ST_BAD_J;
-                if (!(fabs(U[0]) + fabs(U[1]) + fabs(dJ) < T(INFINITY))) flags |= ST_NONFINITE;
-            }
-            vel[0][e] = U[0];
-            vel[1][e] = U[1];
-            // Eq. (7) fluxes, Eq. (12) equilibrium: f^eq_q = U/4 + (1/2c)(i Phi_X + j Phi_Y)
-            const T PhiX[6] = {-P11, -P21, -U[0], T(0), -U[1], T(0)};
-            const T PhiY[6] = {-P12, -P22, T(0), -U[0], T(0), -U[1]};
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const T qU = a.quarter * U[k];
-                const T fx = a.inv2c * PhiX[k], fy = a.inv2c * PhiY[k];
-                const T src = (k == 0) ? a.src1 : (k == 1) ? a.src2 : T(0);
-                // Eq. (14): f* = (1 - omega) f + omega f^eq + dt (2 - omega) w B
-                f[0][k][e] = a.one_m_omega * f[0][k][e] + a.omega * (qU + fx) + src;
-                f[2][k][e] = a.one_m_omega * f[2][k][e] + a.omega * (qU - fx) + src;
-                f[1][k][e] = a.one_m_omega * f[1][k][e] + a.omega * (qU + fy) + src;
-                f[3][k][e] = a.one_m_omega * f[3][k][e] + a.omega * (qU - fy) + src;
-            }
+                for (int k = 0; k < 6; ++k) fq[q][k] = f[q][k][e];
+            collide_node<LAW, T>(fq, a, x0 + e < nx, flags, vel[0][e], vel[1][e]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) f[q][k][e] = fq[q][k];
         }
 
         if (act) {
@@ -147,17 +241,17 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    T *dst = fout + (q * 6 + k) * plane + row;
+                    S *dst = fout + (q * 6 + k) * plane + row;
                     if (full) {
                         PK o;
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) o.v[e] = f[q][k][e];
+                        for (int e = 0; e < VEC; ++e) o.v[e] = to_store<S>(f[q][k][e]);
                         *reinterpret_cast<PK *>(dst) = o;
                     } else {
                         // ragged end: never write past node nx - 1 (column nx is a ghost cell)
 #pragma unroll
                         for (int e = 0; e < VEC; ++e)
-                            if (x0 + e < nx) dst[e] = f[q][k][e];
+                            if (x0 + e < nx) dst[e] = to_store<S>(f[q][k][e]);
                     }
                 }
             // Eq. (22): u*^{n+1} = u*^n + dt v^n (the two half steps of the paper)
@@ -169,105 +263,174 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
                 for (int e = 0; e < VEC; ++e) u.v[e] += a.dt * (double)vel[c][e];
                 *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
             }
+            if (FUSE) lane_ghosts<LAW, S, VEC>(a, fout, row, x0, y, flags);
+        }
+    }
+    flags = __reduce_or_sync(FULL_MASK, flags);
+    if (flags && lane == 0) atomicOr(a.status, (int)flags);
+}
 
-            if (FUSE) {
-                // ---- bottom ghost row (plane q=1, row y = -1) and top ghost row
-                // (plane q=3, row y = ny): whole vectors, one per lane
-                const bool ypers = a.kind[EDGE_BOTTOM] == BC_PERIODIC;
+// 16-bit storage (FP16, BF16): V = 4 or 8 nodes per lane, loaded as 8- or
+// 16-byte vectors and kept packed in registers (two values per 32-bit word),
+// so a lane holds half the registers of an unpacked vector. The one-column
+// shifts of the +x and -x populations are funnel shifts of packed words; each
+// node is unpacked, collided in FP32 and packed back in place.
+__device__ __forceinline__ float unpack16(unsigned w, int hi, __half)
+{
+    return __half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xffffu))));
+}
+__device__ __forceinline__ float unpack16(unsigned w, int hi, __nv_bfloat16)
+{
+    return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+}
+template <typename S>
+__device__ __forceinline__ unsigned bits16(float v);
+template <>
+__device__ __forceinline__ unsigned bits16<__half>(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <>
+__device__ __forceinline__ unsigned bits16<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+template <int W>
+struct Words {
+    unsigned w[W];
+};
+
+template <typename S, int LAW, int V, bool FUSE>
+__global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
+{
+    constexpr int W = V / 2;  // 32-bit words per vector
+    using WV = Words<W>;
+    using PD = Pack<double, 4>;
+    static_assert(V == 4 || V == 8, "4 or 8 nodes per lane");
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int nw = gridDim.x * wpb;
+    const int nx = a.L.nx, ny = a.L.ny;
+    const int segw = 32 * V;
+    const int nseg = (nx + segw - 1) / segw;
+    const int ntask = ny * nseg;
+    const long long plane = a.L.plane;
+    const int pitch = a.L.pitch;
+    const unsigned short *__restrict__ fin = static_cast<const unsigned short *>(a.fin);
+    unsigned short *__restrict__ fout = static_cast<unsigned short *>(a.fout);
+    auto ldv = [&](const unsigned short *p) {
+        WV r;
+        if constexpr (W == 2) {
+            const uint2 t = *reinterpret_cast<const uint2 *>(p);
+            r.w[0] = t.x;
+            r.w[1] = t.y;
+        } else {
+            const uint4 t = *reinterpret_cast<const uint4 *>(p);
+            r.w[0] = t.x;
+            r.w[1] = t.y;
+            r.w[2] = t.z;
+            r.w[3] = t.w;
+        }
+        return r;
+    };
+    auto stv = [&](unsigned short *p, const WV &r) {
+        if constexpr (W == 2)
+            *reinterpret_cast<uint2 *>(p) = make_uint2(r.w[0], r.w[1]);
+        else
+            *reinterpret_cast<uint4 *>(p) = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
+    };
+
+    unsigned flags = 0;
+    for (int task = gw; task < ntask; task += nw) {
+        int y, seg;
+        task_coords(task, nseg, y, seg);
+        const int x0 = seg * segw + lane * V;
+        const bool act = x0 < nx;
+        const bool ld0 = x0 <= nx;
+        const long long row = (long long)(y + 1) * pitch + a.L.xoff + x0;
+
+        WV w[4][6];  // element e of plane (q, k) in half e & 1 of word e >> 1
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int e_id = side == 0 ? EDGE_BOTTOM : EDGE_TOP;
-                    const int qd = side == 0 ? 1 : 3;          // missing direction
-                    const int qo = side == 0 ? 3 : 1;          // outgoing direction -d
-                    const int yb = side == 0 ? 0 : ny - 1;     // boundary row
-                    const int ysrc = side == 0 ? ny - 1 : 0;   // periodic source row
-                    const long long grow = (long long)(side == 0 ? 0 : ny + 1) * pitch + a.L.xoff + x0;
-                    T *dst = fout + (long long)(qd * 6) * plane + grow;
-                    if (ypers) {
-                        if (y == ysrc)
+        for (int k = 0; k < 6; ++k) {
+            WV c0 = {}, c1 = {}, c2 = {}, c3 = {};
+            if (ld0) {
+                c0 = ldv(fin + (0 * 6 + k) * plane + row);
+                c2 = ldv(fin + (2 * 6 + k) * plane + row);
+            }
+            if (act) {
+                c1 = ldv(fin + (1 * 6 + k) * plane + row - pitch);
+                c3 = ldv(fin + (3 * 6 + k) * plane + row + pitch);
+            }
+            // +x: element e comes from x - 1, i.e. element e - 1 of this lane
+            // (element V-1 of the previous lane for e = 0, carried in the high half)
+            unsigned lw = __shfl_up_sync(FULL_MASK, c0.w[W - 1], 1);
+            if (act && lane == 0) lw = (unsigned)fin[(0 * 6 + k) * plane + row - 1] << 16;
+            w[0][k].w[0] = __funnelshift_l(lw, c0.w[0], 16);
 #pragma unroll
-                            for (int k = 0; k < 6; ++k) {
-                                PK o;
+            for (int i = 1; i < W; ++i) w[0][k].w[i] = __funnelshift_l(c0.w[i - 1], c0.w[i], 16);
+            // -x: element e comes from x + 1 (element 0 of the next lane for e = V-1)
+            unsigned rw = __shfl_down_sync(FULL_MASK, c2.w[0], 1);
+            if (act && lane == 31) rw = (unsigned)fin[(2 * 6 + k) * plane + row + V];
 #pragma unroll
-                                for (int e = 0; e < VEC; ++e) o.v[e] = f[qd][k][e];
-                                *reinterpret_cast<PK *>(dst + k * plane) = o;
-                            }
-                    } else if (y == yb) {
-                        T g[6][VEC];
+            for (int i = 0; i < W - 1; ++i) w[2][k].w[i] = __funnelshift_r(c2.w[i], c2.w[i + 1], 16);
+            w[2][k].w[W - 1] = __funnelshift_r(c2.w[W - 1], rw, 16);
+            w[1][k] = c1;  // from y - 1
+            w[3][k] = c3;  // from y + 1
+        }
+        // u* is read together with the populations so that its latency
+        // overlaps theirs instead of following the collision
+        const long long urow = (long long)y * a.L.upitch + x0;
+        PD u[2][V / 4];
+        if (act)
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) {
-                            T out[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                            if (x0 + e < nx) {
-                                T fo[6], f0[6], f1[6], f2[6], f3[6], U[6];
+            for (int c = 0; c < 2; ++c)
 #pragma unroll
-                                for (int k = 0; k < 6; ++k) {
-                                    fo[k] = f[qo][k][e];
-                                    f0[k] = f[0][k][e]; f1[k] = f[1][k][e]; f2[k] = f[2][k][e]; f3[k] = f[3][k][e];
-                                }
-                                state_from_fstar(f0, f1, f2, f3, a.hdtb1, a.hdtb2, U);
-                                double val[2];
-                                const double gt = timefn(a.timefn[e_id], a.tp[e_id], th) *
-                                                  (a.profile[e_id] ? a.profile[e_id][x0 + e] : 1.0);
-                                val[0] = a.value[e_id][0] * gt;
-                                val[1] = a.value[e_id][1] * gt;
-                                edge_ghost<LAW, T>(e_id, a.kind[e_id], fo, U, val, a.c, a.lam, a.mu, out, flags);
-                            }
+                for (int h = 0; h < V / 4; ++h) u[c][h] = *reinterpret_cast<const PD *>(a.ustar + c * a.L.uplane + urow + 4 * h);
+
+        float vel[2][V];
 #pragma unroll
-                            for (int k = 0; k < 6; ++k) g[k][e] = out[k];
-                        }
+        for (int e = 0; e < V; ++e) {
+            float fq[4][6];
 #pragma unroll
-                        for (int k = 0; k < 6; ++k) {
-                            PK o;
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) o.v[e] = g[k][e];
-                            *reinterpret_cast<PK *>(dst + k * plane) = o;
-                        }
-                    }
+                for (int k = 0; k < 6; ++k) fq[q][k] = unpack16(w[q][k].w[e >> 1], e & 1, S());
+            collide_node<LAW, float>(fq, a, x0 + e < nx, flags, vel[0][e], vel[1][e]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    unsigned &ww = w[q][k].w[e >> 1];
+                    const unsigned b = bits16<S>(fq[q][k]);
+                    ww = (e & 1) ? __byte_perm(ww, b, 0x5410) : __byte_perm(ww, b, 0x3254);
                 }
-                // ---- left ghost column (plane 0, x = -1) and right ghost column
-                // (plane 2, x = nx): one element of one lane per row
-                const bool xpers = a.kind[EDGE_LEFT] == BC_PERIODIC;
-                const long long rbase = (long long)(y + 1) * pitch + a.L.xoff;
-                const int elast = nx - 1 - x0;  // element of node nx - 1 in this lane, if any
+        }
+
+        if (act) {
+            const bool full = x0 + V <= nx;
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int e_id = side == 0 ? EDGE_LEFT : EDGE_RIGHT;
-                    const int qd = side == 0 ? 0 : 2, qo = side == 0 ? 2 : 0;
-                    const int gx = side == 0 ? -1 : nx;
-                    // element holding the boundary node (left: x = 0, right: x = nx-1)
-                    // and, for periodic edges, the source node on the opposite side
-                    const int eb = side == 0 ? (x0 == 0 ? 0 : -1) : (elast >= 0 && elast < VEC ? elast : -1);
-                    const int es = side == 0 ? (elast >= 0 && elast < VEC ? elast : -1) : (x0 == 0 ? 0 : -1);
-                    T *dst = fout + (long long)(qd * 6) * plane + rbase + gx;
-                    if (xpers) {
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e)
-                            if (e == es)
-#pragma unroll
-                                for (int k = 0; k < 6; ++k) dst[k * plane] = f[qd][k][e];
+                for (int k = 0; k < 6; ++k) {
+                    unsigned short *dst = fout + (q * 6 + k) * plane + row;
+                    if (full) {
+                        stv(dst, w[q][k]);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e)
-                            if (e == eb) {
-                                T fo[6], f0[6], f1[6], f2[6], f3[6], U[6], out[6];
-#pragma unroll
-                                for (int k = 0; k < 6; ++k) {
-                                    fo[k] = f[qo][k][e];
-                                    f0[k] = f[0][k][e]; f1[k] = f[1][k][e]; f2[k] = f[2][k][e]; f3[k] = f[3][k][e];
-                                }
-                                state_from_fstar(f0, f1, f2, f3, a.hdtb1, a.hdtb2, U);
-                                double val[2];
-                                const double gt = timefn(a.timefn[e_id], a.tp[e_id], th) *
-                                                  (a.profile[e_id] ? a.profile[e_id][y] : 1.0);
-                                val[0] = a.value[e_id][0] * gt;
-                                val[1] = a.value[e_id][1] * gt;
-                                edge_ghost<LAW, T>(e_id, a.kind[e_id], fo, U, val, a.c, a.lam, a.mu, out, flags);
-#pragma unroll
-                                for (int k = 0; k < 6; ++k) dst[k * plane] = out[k];
-                            }
+                        for (int e = 0; e < V; ++e) {
+                            const unsigned ww = w[q][k].w[e >> 1];
+                            if (x0 + e < nx) dst[e] = (unsigned short)((e & 1) ? (ww >> 16) : (ww & 0xffffu));
+                        }
                     }
                 }
-            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int h = 0; h < V / 4; ++h) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) u[c][h].v[e] += a.dt * (double)vel[c][4 * h + e];
+                    *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow + 4 * h) = u[c][h];
+                }
+            if (FUSE) lane_ghosts<LAW, S, V>(a, reinterpret_cast<S *>(fout), row, x0, y, flags);
         }
     }
     flags = __reduce_or_sync(FULL_MASK, flags);
@@ -277,10 +440,11 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<T> a)
 // Ghost refresh in the node form (after initialization, a checkpoint load or
 // new edge data): the same values the fused step writes, from the stored
 // post-collision populations of the current buffer.
-template <typename T, int LAW>
+template <typename S, int LAW>
 __global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
 {
-    T *f = static_cast<T *>(a.f);
+    using T = typename Prec<S>::R;
+    S *f = static_cast<S *>(a.f);
     int e = 0;
     while (e < 3 && (int)blockIdx.x >= a.blk_end[e]) ++e;
     const int b0 = e ? a.blk_end[e - 1] : 0;
@@ -310,17 +474,17 @@ __global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) fq[q][k] = f[idx(q, k, xb, yb)];
+        for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(f[idx(q, k, xb, yb)]);
     state_from_fstar(fq[0], fq[1], fq[2], fq[3], (T)a.hdtb1, (T)a.hdtb2, U);
 #pragma unroll
     for (int k = 0; k < 6; ++k) fo[k] = fq[md][k];
     double val[2];
-    edge_value(E, s, ((double)(*a.step) + 0.5) * a.dt, val);
+    edge_value(E, s, a.g[e], val);
     unsigned flags = 0;
     edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, (T)a.m.lam, (T)a.m.mu, out, flags);
     if (flags) atomicOr(a.status, (int)flags);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = out[k];
+    for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = to_store<S>(out[k]);
 }
 
 // ---------------------------------------------------------------- edges
@@ -354,7 +518,7 @@ __device__ void node_state(const EdgeView<T> &v, int x, int y, double hb1, doubl
     for (int k = 0; k < 6; ++k) {
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) s += (double)v.f[v.idx(q, k, x, y)];
+        for (int q = 0; q < 4; ++q) s += (double)ld_r(v.f[v.idx(q, k, x, y)]);
         U[k] = s;
     }
     U[0] -= hb1;
@@ -515,10 +679,9 @@ __global__ void __launch_bounds__(128) k_edges(const EdgeArgs a)
         for (int k = 0; k < 6; ++k) v.f[v.idx(d, k, gx, gy)] = v.f[v.idx(d, k, sx, sy)];
         return;
     }
-    // edge data at t^n + dt/2 (Eq. 23); *step counts the steps already taken
-    const double th = ((double)(*a.step) + 0.5) * a.dt;
-    const double g = timefn(E.timefn, E.tp, th) * (E.profile ? E.profile[s] : 1.0);
-    const double val[2] = {E.value[0] * g, E.value[1] * g};
+    // edge data at t^n + dt/2 (Eq. 23)
+    double val[2];
+    edge_value(E, s, a.g[e], val);
     double D[6], S[6];
     if (E.kind == BC_VELOCITY) {
         // Eq. (24); the F-components have D = +1, so the rest offset cancels
@@ -540,81 +703,89 @@ __global__ void __launch_bounds__(128) k_edges(const EdgeArgs a)
         for (int m = 0; m < 4; ++m) S[2 + m] = 0.5 * Gb[m];
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v.f[v.idx(d, k, gx, gy)] = (T)(D[k] * (double)v.f[v.idx(md, k, xb, yb)] + S[k]);
+    for (int k = 0; k < 6; ++k)
+        v.f[v.idx(d, k, gx, gy)] = to_store<T>(D[k] * (double)ld_r(v.f[v.idx(md, k, xb, yb)]) + S[k]);
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename T, int LAW, int VEC>
-static cudaError_t launch_step_t(const StepArgs<T> &a, bool fuse, int grid, cudaStream_t st)
+template <typename S, int LAW>
+static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
 {
-    if (fuse)
-        k_step<T, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
-    else
-        k_step<T, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
+    if constexpr (sizeof(S) == 2) {
+        if (fuse)
+            k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);
+        else
+            k_step16<S, LAW, STEP16_V, false><<<grid, 128, 0, st>>>(a);
+    } else {
+        constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors
+        if (fuse)
+            k_step<S, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
+        else
+            k_step<S, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_step_law(int law, const StepArgs<T> &a, bool fuse, int grid, cudaStream_t st)
+template <typename S>
+static cudaError_t launch_step_law(int law, const void *args, bool fuse, int grid, cudaStream_t st)
 {
-    constexpr int VEC = 16 / sizeof(T);
+    const auto &a = *static_cast<const StepArgs<typename Prec<S>::R> *>(args);
     switch (law) {
-    case LAW_SVK: return launch_step_t<T, LAW_SVK, VEC>(a, fuse, grid, st);
-    case LAW_NH: return launch_step_t<T, LAW_NH, VEC>(a, fuse, grid, st);
-    default: return launch_step_t<T, LAW_LOGNH, VEC>(a, fuse, grid, st);
+    case LAW_SVK: return launch_step_t<S, LAW_SVK>(a, fuse, grid, st);
+    case LAW_NH: return launch_step_t<S, LAW_NH>(a, fuse, grid, st);
+    default: return launch_step_t<S, LAW_LOGNH>(a, fuse, grid, st);
     }
 }
 
-cudaError_t launch_step(int storage_bytes, int law, bool fuse, const void *args, int grid, cudaStream_t st)
+cudaError_t launch_step(int storage, int law, bool fuse, const void *args, int grid, cudaStream_t st)
 {
-    if (storage_bytes == 8)
-        return launch_step_law<double>(law, *static_cast<const StepArgs<double> *>(args), fuse, grid, st);
-    return launch_step_law<float>(law, *static_cast<const StepArgs<float> *>(args), fuse, grid, st);
+    return with_storage(storage, [&](auto tag) {
+        return launch_step_law<decltype(tag)>(law, args, fuse, grid, st);
+    });
 }
 
-cudaError_t launch_edges(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st)
-{
-    if (grid <= 0) return cudaSuccess;
-    if (storage_bytes == 8)
-        k_edges<double><<<grid, 128, 0, st>>>(a);
-    else
-        k_edges<float><<<grid, 128, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t launch_ghosts_t(const EdgeArgs &a, int grid, cudaStream_t st)
-{
-    switch (a.m.law) {
-    case LAW_SVK: k_ghosts<T, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
-    case LAW_NH: k_ghosts<T, LAW_NH><<<grid, 128, 0, st>>>(a); break;
-    default: k_ghosts<T, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ghosts(int storage_bytes, const EdgeArgs &a, int grid, cudaStream_t st)
+cudaError_t launch_edges(int storage, const EdgeArgs &a, int grid, cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    return storage_bytes == 8 ? launch_ghosts_t<double>(a, grid, st) : launch_ghosts_t<float>(a, grid, st);
+    return with_storage(storage, [&](auto tag) {
+        k_edges<decltype(tag)><<<grid, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
-int step_blocks_per_sm(int storage_bytes, int law)
+cudaError_t launch_ghosts(int storage, const EdgeArgs &a, int grid, cudaStream_t st)
 {
-    int n = 0;
-    const void *fn;
-    if (storage_bytes == 8)
-        fn = (law == LAW_SVK) ? (const void *)k_step<double, LAW_SVK, 2, true>
-             : (law == LAW_NH) ? (const void *)k_step<double, LAW_NH, 2, true>
-                               : (const void *)k_step<double, LAW_LOGNH, 2, true>;
-    else
-        fn = (law == LAW_SVK) ? (const void *)k_step<float, LAW_SVK, 4, true>
-             : (law == LAW_NH) ? (const void *)k_step<float, LAW_NH, 4, true>
-                               : (const void *)k_step<float, LAW_LOGNH, 4, true>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
-    return n;
+    if (grid <= 0) return cudaSuccess;
+    return with_storage(storage, [&](auto tag) {
+        using S = decltype(tag);
+        switch (a.m.law) {
+        case LAW_SVK: k_ghosts<S, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
+        case LAW_NH: k_ghosts<S, LAW_NH><<<grid, 128, 0, st>>>(a); break;
+        default: k_ghosts<S, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
+        }
+        return cudaGetLastError();
+    });
 }
 
-int step_vec(int storage_bytes) { return 16 / storage_bytes; }
+int step_blocks_per_sm(int storage, int law)
+{
+    return with_storage(storage, [&](auto tag) {
+        using S = decltype(tag);
+        const void *fn;
+        if constexpr (sizeof(S) == 2)
+            fn = (law == LAW_SVK) ? (const void *)k_step16<S, LAW_SVK, STEP16_V, true>
+                 : (law == LAW_NH) ? (const void *)k_step16<S, LAW_NH, STEP16_V, true>
+                                   : (const void *)k_step16<S, LAW_LOGNH, STEP16_V, true>;
+        else
+            fn = (law == LAW_SVK) ? (const void *)k_step<S, LAW_SVK, 16 / sizeof(S), true>
+                 : (law == LAW_NH) ? (const void *)k_step<S, LAW_NH, 16 / sizeof(S), true>
+                                   : (const void *)k_step<S, LAW_LOGNH, 16 / sizeof(S), true>;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
+        return n;
+    });
+}
+
+int step_vec(int storage) { return storage == STORE_F64 ? 2 : storage == STORE_F32 ? 4 : STEP16_V; }
 
 } // namespace tlv

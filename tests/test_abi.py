@@ -54,7 +54,7 @@ def test_library_links_no_torch(lbm):
     (dict(nx=8, ny=8, c=-1.0), "LBM_ERR_ARG"),
     (dict(nx=8, ny=8, dx=0.0), "LBM_ERR_ARG"),
     (dict(nx=8, ny=8, storage=7), "LBM_ERR_ARG"),
-    (dict(nx=8, ny=8, storage=2), "LBM_ERR_UNSUPPORTED"),
+    (dict(nx=8, ny=8, storage=4), "LBM_ERR_ARG"),
     (dict(nx=1 << 25, ny=8), "LBM_ERR_ARG"),
 ])
 def test_create_rejects_bad_configs_before_touching_the_device(lbm, kw, err):
