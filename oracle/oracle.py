@@ -37,6 +37,9 @@ def _load():
         lib.orc_set_body_force.argtypes = [C.c_void_p, C.c_double, C.c_double]
         lib.orc_set_fb_mode.argtypes = [C.c_void_p, C.c_int]
         lib.orc_set_body_force_field.argtypes = [C.c_void_p, _dp]
+        lib.orc_set_material_field.argtypes = [C.c_void_p, _dp, C.c_double]
+        lib.orc_adjoint.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_long), C.c_int,
+                                    C.POINTER(C.c_int), _dp, _dp, _dp, _dp]
         lib.orc_set_edge.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp]
         lib.orc_set_edge_data.argtypes = [C.c_void_p, C.c_int, _dp]
         lib.orc_init.argtypes = [C.c_void_p, _dp, _dp, C.c_int, _dp, _dp]
@@ -177,6 +180,33 @@ class Lattice:
     def set_body_force_field(self, b):
         p, _k = _p(None if b is None else np.asarray(b).reshape(2, self.ny, self.nx))
         self._lib.orc_set_body_force_field(self._h, p)
+
+    def set_material_field(self, mu, lam_ratio):
+        """Per-node shear modulus (ny, nx) with lambda = lam_ratio * mu (SVK, NH,
+        LOGNH; after set_law); None reverts to the uniform parameters."""
+        p, _k = _p(None if mu is None else np.asarray(mu).reshape(self.ny, self.nx))
+        if self._lib.orc_set_material_field(self._h, p, lam_ratio) != 0:
+            raise ValueError("bad material field")
+
+    def adjoint(self, U0, nsteps, sens, rec_steps, target, order=2):
+        """Reference adjoint of L = 1/2 sum_k sum_s |u(X_s, t^{n_k}) - d_{k,s}|^2.
+        sens: node indices iy * nx + ix; rec_steps: recorded steps; target:
+        (len(rec_steps), len(sens), 2). Returns (L, dL/dmu (ny, nx), dL/dv0
+        (2, ny, nx))."""
+        a, _k1 = _p(np.asarray(U0).reshape(6, self.ny, self.nx))
+        sens = np.ascontiguousarray(sens, dtype=np.int64)
+        rec = np.ascontiguousarray(rec_steps, dtype=np.int32)
+        tg, _k2 = _p(np.asarray(target).reshape(len(rec), len(sens), 2))
+        loss = np.zeros(1)
+        gmu = np.zeros((self.ny, self.nx))
+        gv0 = np.zeros((2, self.ny, self.nx))
+        rc = self._lib.orc_adjoint(self._h, a, order, int(nsteps), len(sens),
+                                   sens.ctypes.data_as(C.POINTER(C.c_long)), len(rec),
+                                   rec.ctypes.data_as(C.POINTER(C.c_int)), tg, loss.ctypes.data_as(_dp),
+                                   gmu.ctypes.data_as(_dp), gv0.ctypes.data_as(_dp))
+        if rc != 0:
+            raise RuntimeError("orc_adjoint failed with %d" % rc)
+        return float(loss[0]), gmu, gv0
 
     def edge_len(self, e):
         return self.ny if e in (LEFT, RIGHT) else self.nx

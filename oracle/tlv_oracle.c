@@ -300,6 +300,8 @@ struct orc {
     double dx, c, omega, dt;
     int law;
     double prm[8];
+    double *mufield; /* per-node mu (N) with lambda = lam_ratio * mu, or NULL */
+    double lam_ratio;
     double b[2];
     double *bfield; /* 2N or NULL */
     orc_edge e[4];
@@ -316,6 +318,18 @@ static int edge_len(const orc *o, int e) { return (e == ORC_LEFT || e == ORC_RIG
 static int xper(const orc *o) { return o->e[ORC_LEFT].kind == ORC_PERIODIC; }
 static int yper(const orc *o) { return o->e[ORC_BOTTOM].kind == ORC_PERIODIC; }
 static double bforce(const orc *o, int comp, long n) { return o->bfield ? o->bfield[comp * o->N + n] : o->b[comp]; }
+
+/* material parameters of node n: the uniform set, or {lam_ratio mu_n, mu_n}
+ * when a shear-modulus field is set */
+static const double *node_prm(const orc *o, long n, double buf[8])
+{
+    int i;
+    if (!o->mufield) return o->prm;
+    for (i = 0; i < 8; ++i) buf[i] = 0.0;
+    buf[0] = o->lam_ratio * o->mufield[n];
+    buf[1] = o->mufield[n];
+    return buf;
+}
 
 orc *orc_new(int nx, int ny, double dx, double c, double omega)
 {
@@ -353,6 +367,7 @@ void orc_free(orc *o)
         free(o->e[e].data);
     }
     free(o->bfield);
+    free(o->mufield);
     free(o->f);
     free(o->fs);
     free(o->U);
@@ -366,6 +381,23 @@ int orc_set_law(orc *o, int law, const double *prm, int nprm)
     if (law < ORC_SVK || law > ORC_GENT || nprm < 2 || nprm > 8) return -1;
     o->law = law;
     for (i = 0; i < 8; ++i) o->prm[i] = (i < nprm) ? prm[i] : 0.0;
+    free(o->mufield); /* a new law drops a shear-modulus field */
+    o->mufield = NULL;
+    return 0;
+}
+
+int orc_set_material_field(orc *o, const double *mu_N, double lam_ratio)
+{
+    long n;
+    free(o->mufield);
+    o->mufield = NULL;
+    if (!mu_N) return 0;
+    if (o->law != ORC_SVK && o->law != ORC_NH && o->law != ORC_LOGNH) return -1;
+    for (n = 0; n < o->N; ++n)
+        if (!(mu_N[n] > 0.0)) return -2;
+    o->mufield = (double *)malloc((size_t)o->N * sizeof(double));
+    memcpy(o->mufield, mu_N, (size_t)o->N * sizeof(double));
+    o->lam_ratio = lam_ratio;
     return 0;
 }
 
@@ -470,10 +502,11 @@ int orc_init(orc *o, const double *U0, const double *u0, int order, const double
     for (iy = 0; iy < o->ny; ++iy)
         for (ix = 0; ix < o->nx; ++ix) {
             const long n = nid(o, ix, iy);
-            double U[6], F[4], P[4], feq[24];
+            double U[6], F[4], P[4], feq[24], pb[8];
+            const double *prm = node_prm(o, n, pb);
             for (k = 0; k < 6; ++k) U[k] = U0[k * N + n];
             for (m = 0; m < 4; ++m) F[m] = U[2 + m];
-            if (orc_piola(o->law, o->prm, F, P) != 0) o->status |= ORC_BAD_J;
+            if (orc_piola(o->law, prm, F, P) != 0) o->status |= ORC_BAD_J;
             orc_feq(U, P, c, feq);
             for (q = 0; q < 4; ++q)
                 for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = feq[q * 6 + k];
@@ -484,7 +517,7 @@ int orc_init(orc *o, const double *U0, const double *u0, int order, const double
                     gX[k] = dUdX ? dUdX[k * N + n] : fd(o, U0 + k * N, ix, iy, 0);
                     gY[k] = dUdY ? dUdY[k * N + n] : fd(o, U0 + k * N, ix, iy, 1);
                 }
-                orc_tangent(o->law, o->prm, F, Ct);
+                orc_tangent(o->law, prm, F, Ct);
                 /* d_alpha P_iA = C_iAkB d_alpha F_kB (text after Eq. 18) */
                 for (m = 0; m < 4; ++m) {
                     dPX[m] = 0.0;
@@ -555,11 +588,11 @@ static double dT(const orc *o, int e, int L, int s, int comp)
 
 /* r_i = P_iA(F) N_A - T_i on an edge whose normal is material direction a
  * with sign Na */
-static void traction_residual(const orc *o, const double F[4], int a, double Na, const double T[2],
-                              double r[2])
+static void traction_residual(const orc *o, const double *prm, const double F[4], int a, double Na,
+                              const double T[2], double r[2])
 {
     double P[4];
-    orc_piola(o->law, o->prm, F, P);
+    orc_piola(o->law, prm, F, P);
     r[0] = Na * P[0 * 2 + a] - T[0];
     r[1] = Na * P[1 * 2 + a] - T[1];
 }
@@ -571,6 +604,8 @@ static int boundary_F(orc *o, int e, int s, const double T[2], double Fb[4])
     const int tc = 1 - a;                                    /* tangential column index */
     const double Na = (e == ORC_LEFT || e == ORC_BOTTOM) ? -1.0 : 1.0;
     const long n0 = edge_node(o, e, 0, s), n1 = (o->fb_mode == ORC_FB_EXTRAP2) ? edge_node(o, e, 1, s) : n0;
+    double pb[8];
+    const double *prm = node_prm(o, n0, pb);
     const double tmax = fmax(fabs(T[0]), fabs(T[1]));
     const double tol = 1e-13 * (tmax > 1.0 ? tmax : 1.0);
     double r[2];
@@ -586,12 +621,12 @@ static int boundary_F(orc *o, int e, int s, const double T[2], double Fb[4])
         }
         Fb[i * 2 + a] = o->U[(2 + i * 2 + a) * o->N + n0]; /* Newton starting point */
     }
-    traction_residual(o, Fb, a, Na, T, r);
+    traction_residual(o, prm, Fb, a, Na, T, r);
     for (it = 0; it < 20; ++it) {
         double Ct[16], Jac[4], det, d0, d1, rn, alpha = 1.0;
         int accepted = 0;
         if (fmax(fabs(r[0]), fabs(r[1])) <= tol) return 0;
-        orc_tangent(o->law, o->prm, Fb, Ct);
+        orc_tangent(o->law, prm, Fb, Ct);
         /* d r_i / d F_ka = Na C_iaka */
         for (i = 0; i < 2; ++i) {
             Jac[i * 2 + 0] = Na * Ct[(i * 2 + a) * 4 + (0 * 2 + a)];
@@ -607,7 +642,7 @@ static int boundary_F(orc *o, int e, int s, const double T[2], double Fb[4])
             Ft[0 * 2 + a] += alpha * d0;
             Ft[1 * 2 + a] += alpha * d1;
             if (Ft[0] * Ft[3] - Ft[1] * Ft[2] > 0.0) {
-                traction_residual(o, Ft, a, Na, T, rt);
+                traction_residual(o, prm, Ft, a, Na, T, rt);
                 if (hypot(rt[0], rt[1]) < rn) {
                     memcpy(Fb, Ft, sizeof Ft);
                     r[0] = rt[0];
@@ -658,10 +693,10 @@ int orc_step(orc *o, int nsteps)
         /* 2-3. P(F^n), fluxes, equilibrium and BGK collision with the
          * trapezoidal source, Eq. (14) with w_ij = 1/8 */
         for (n = 0; n < N; ++n) {
-            double U[6], F[4], P[4], feq[24];
+            double U[6], F[4], P[4], feq[24], pb[8];
             for (k = 0; k < 6; ++k) U[k] = o->U[k * N + n];
             for (k = 0; k < 4; ++k) F[k] = U[2 + k];
-            if (orc_piola(o->law, o->prm, F, P) != 0) o->status |= ORC_BAD_J;
+            if (orc_piola(o->law, node_prm(o, n, pb), F, P) != 0) o->status |= ORC_BAD_J;
             for (k = 0; k < 6; ++k)
                 if (!isfinite(U[k])) o->status |= ORC_NONFINITE;
             orc_feq(U, P, c, feq);
@@ -745,7 +780,7 @@ void orc_state(const orc *o, double *U, double *P, double *sigma)
     long n;
     int q, k;
     for (n = 0; n < N; ++n) {
-        double u6[6], F[4], Pn[4], J;
+        double u6[6], F[4], Pn[4], J, pb[8];
         for (k = 0; k < 6; ++k) {
             double sum = 0.0;
             for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
@@ -754,7 +789,7 @@ void orc_state(const orc *o, double *U, double *P, double *sigma)
             if (U) U[k * N + n] = sum;
         }
         for (k = 0; k < 4; ++k) F[k] = u6[2 + k];
-        orc_piola(o->law, o->prm, F, Pn);
+        orc_piola(o->law, node_prm(o, n, pb), F, Pn);
         if (P)
             for (k = 0; k < 4; ++k) P[k * N + n] = Pn[k];
         if (sigma) {
@@ -789,3 +824,320 @@ int orc_status(const orc *o) { return o->status; }
 long orc_step_count(const orc *o) { return o->step; }
 double orc_time(const orc *o) { return o->step * o->dt; }
 double orc_dt(const orc *o) { return o->dt; }
+
+/* ======================================================================
+ * Reference adjoint (the paper has none): the exact discrete adjoint of the
+ * steps above, for the loss
+ *   L = 1/2 sum_k sum_s |u(X_s, t^{n_k}) - d_{k,s}|^2
+ * of displacements u^n = u*^n + (dt/2) v^n (Eq. 22) at sensor nodes X_s and
+ * recorded steps n_k, with respect to the per-node shear modulus mu (lambda =
+ * lam_ratio mu) and the initial velocity v0. Plain reverse sweep over stored
+ * forward states, one phase of the step at a time in reverse order, each
+ * phase transposed from its own definition:
+ *   collision  local 24 x 24 Jacobian of Eq. (14) by the complex step, and
+ *              the exact mu-derivative of an affine map (central difference);
+ *   streaming  the transposed permutation of Eq. (15);
+ *   edges      Eq. (23) with D and S; for a traction edge the implicit
+ *              function theorem on N_a P_ia(F^b) = T_i (Sec. 3.6.2) gives
+ *              how the normal column of F^b moves with the node's tangential
+ *              column and with mu;
+ *   quadrature Eq. (22);
+ *   init       Eqs. (16)-(21) are linear in v0 and affine in each node's mu
+ *              (P and C are linear in (lambda, mu) for SVK, NH and log-NH), so
+ *              their Jacobian columns are exact central differences.
+ * Node form of F^b only. Memory: every f^n is kept (small lattices only).
+ * ====================================================================== */
+
+/* Eq. (14) at one node in complex arithmetic (for the complex-step Jacobian) */
+static void collide_c(const orc *o, const double *prm, double b1, double b2, const double complex f[24],
+                      double complex fs[24])
+{
+    const double c = o->c, dt = o->dt, w = o->omega;
+    double complex U[6], F[4], P[4], PhiX[6], PhiY[6];
+    int q, k;
+    for (k = 0; k < 6; ++k) {
+        U[k] = 0.0;
+        for (q = 0; q < 4; ++q) U[k] += f[q * 6 + k];
+    }
+    U[0] += 0.5 * dt * b1;
+    U[1] += 0.5 * dt * b2;
+    for (k = 0; k < 4; ++k) F[k] = U[2 + k];
+    piola_c(o->law, prm, F, P);
+    PhiX[0] = -P[0]; PhiX[1] = -P[2]; PhiX[2] = -U[0]; PhiX[3] = 0.0; PhiX[4] = -U[1]; PhiX[5] = 0.0;
+    PhiY[0] = -P[1]; PhiY[1] = -P[3]; PhiY[2] = 0.0; PhiY[3] = -U[0]; PhiY[4] = 0.0; PhiY[5] = -U[1];
+    for (q = 0; q < 4; ++q)
+        for (k = 0; k < 6; ++k) {
+            const double complex feq = 0.25 * (U[k] + (2.0 / c) * (CI[q] * PhiX[k] + CJ[q] * PhiY[k]));
+            const double Bk = (k == 0) ? b1 : (k == 1) ? b2 : 0.0;
+            fs[q * 6 + k] = f[q * 6 + k] + w * (feq - f[q * 6 + k]) + dt * (2.0 - w) * 0.125 * Bk;
+        }
+}
+
+/* U^n of every node from o->f into o->U (Eq. 10) */
+static void recover_all(orc *o)
+{
+    const long N = o->N;
+    long n;
+    int q, k;
+    for (n = 0; n < N; ++n)
+        for (k = 0; k < 6; ++k) {
+            double sum = 0.0;
+            for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
+            if (k < 2) sum += 0.5 * o->dt * bforce(o, k, n);
+            o->U[k * N + n] = sum;
+        }
+}
+
+/* 2 x 2 solve A^T z = b */
+static void solve2t(const double A[4], const double b[2], double z[2])
+{
+    const double det = A[0] * A[3] - A[1] * A[2];
+    /* A^T = [[A0, A2], [A1, A3]] */
+    z[0] = (A[3] * b[0] - A[2] * b[1]) / det;
+    z[1] = (-A[1] * b[0] + A[0] * b[1]) / det;
+}
+
+int orc_adjoint(orc *o, const double *U0, int order, int nsteps, int nsens, const long *sens, int nrec,
+                const int *rec_steps, const double *target, double *loss, double *g_mu, double *g_v0)
+{
+    const long N = o->N;
+    const double dt = o->dt;
+    static const int dmiss[4] = {0, 2, 1, 3}, dout[4] = {2, 0, 3, 1};
+    double *fh = NULL, *uh = NULL, *fb = NULL, *fbn = NULL, *fsb = NULL, *Ub = NULL, *ub = NULL, *U0p = NULL,
+           *f0p = NULL, *f0m = NULL, *mu_save = NULL;
+    long m;
+    int step, k, q, e, rc = 0;
+    if (!o->mufield || o->fb_mode != ORC_FB_NODE || nsteps < 0) return -1;
+    for (k = 0; k < nrec; ++k)
+        if (rec_steps[k] < 0 || rec_steps[k] > nsteps) return -1;
+    for (k = 0; k < nsens; ++k)
+        if (sens[k] < 0 || sens[k] >= N) return -1;
+    fh = (double *)malloc((size_t)(nsteps + 1) * 24 * N * sizeof(double));
+    uh = (double *)malloc((size_t)(nsteps + 1) * 2 * N * sizeof(double));
+    fb = (double *)calloc((size_t)24 * N, sizeof(double));
+    fbn = (double *)calloc((size_t)24 * N, sizeof(double));
+    fsb = (double *)calloc((size_t)24 * N, sizeof(double));
+    Ub = (double *)calloc((size_t)6 * N, sizeof(double));
+    ub = (double *)calloc((size_t)2 * N, sizeof(double));
+    U0p = (double *)malloc((size_t)6 * N * sizeof(double));
+    f0p = (double *)malloc((size_t)24 * N * sizeof(double));
+    f0m = (double *)malloc((size_t)24 * N * sizeof(double));
+    mu_save = (double *)malloc((size_t)N * sizeof(double));
+    if (!fh || !uh || !fb || !fbn || !fsb || !Ub || !ub || !U0p || !f0p || !f0m || !mu_save) {
+        rc = -2;
+        goto done;
+    }
+    /* forward, keeping every f^n and u*^n */
+    if (orc_init(o, U0, NULL, order, NULL, NULL) != 0) {
+        rc = -3;
+        goto done;
+    }
+    for (step = 0; step <= nsteps; ++step) {
+        if (step > 0) orc_step(o, 1);
+        memcpy(fh + (size_t)step * 24 * N, o->f, (size_t)24 * N * sizeof(double));
+        memcpy(uh + (size_t)step * 2 * N, o->ustar, (size_t)2 * N * sizeof(double));
+    }
+    if (o->status) {
+        rc = -4;
+        goto done;
+    }
+    /* loss */
+    *loss = 0.0;
+    for (k = 0; k < nrec; ++k) {
+        const double *f = fh + (size_t)rec_steps[k] * 24 * N, *us = uh + (size_t)rec_steps[k] * 2 * N;
+        int s2, cc;
+        for (s2 = 0; s2 < nsens; ++s2)
+            for (cc = 0; cc < 2; ++cc) {
+                const long nn = sens[s2];
+                double v = 0.5 * dt * bforce(o, cc, nn), r;
+                for (q = 0; q < 4; ++q) v += f[(long)(q * 6 + cc) * N + nn];
+                r = us[cc * N + nn] + 0.5 * dt * v - target[((size_t)k * nsens + s2) * 2 + cc];
+                *loss += 0.5 * r * r;
+            }
+    }
+    for (m = 0; m < N; ++m) g_mu[m] = 0.0;
+    /* reverse sweep */
+    for (step = nsteps; step >= 0; --step) {
+        /* loss terms of u^step = u*^step + (dt/2) v^step */
+        for (k = 0; k < nrec; ++k) {
+            const double *f = fh + (size_t)step * 24 * N, *us = uh + (size_t)step * 2 * N;
+            int s2, cc;
+            if (rec_steps[k] != step) continue;
+            for (s2 = 0; s2 < nsens; ++s2)
+                for (cc = 0; cc < 2; ++cc) {
+                    const long nn = sens[s2];
+                    double v = 0.5 * dt * bforce(o, cc, nn), r;
+                    for (q = 0; q < 4; ++q) v += f[(long)(q * 6 + cc) * N + nn];
+                    r = us[cc * N + nn] + 0.5 * dt * v - target[((size_t)k * nsens + s2) * 2 + cc];
+                    ub[cc * N + nn] += r;
+                    for (q = 0; q < 4; ++q) fb[(long)(q * 6 + cc) * N + nn] += 0.5 * dt * r;
+                }
+        }
+        if (step == 0) break;
+        /* the forward step (step - 1) -> step, transposed */
+        memcpy(o->f, fh + (size_t)(step - 1) * 24 * N, (size_t)24 * N * sizeof(double));
+        recover_all(o);
+        memset(Ub, 0, (size_t)6 * N * sizeof(double));
+        memset(fsb, 0, (size_t)24 * N * sizeof(double));
+        /* quadrature u*^step = u*^(step-1) + dt v^(step-1): ub passes through */
+        for (m = 0; m < N; ++m)
+            for (k = 0; k < 2; ++k) Ub[k * N + m] += dt * ub[k * N + m];
+        /* streaming: f^step_q(x + e_q) = f*_q(x) */
+        {
+            int ix, iy;
+            for (iy = 0; iy < o->ny; ++iy)
+                for (ix = 0; ix < o->nx; ++ix)
+                    for (q = 0; q < 4; ++q) {
+                        int tx = ix + CI[q], ty = iy + CJ[q];
+                        if (tx < 0 || tx >= o->nx) {
+                            if (!xper(o)) continue;
+                            tx = (tx + o->nx) % o->nx;
+                        }
+                        if (ty < 0 || ty >= o->ny) {
+                            if (!yper(o)) continue;
+                            ty = (ty + o->ny) % o->ny;
+                        }
+                        for (k = 0; k < 6; ++k)
+                            fsb[(long)(q * 6 + k) * N + nid(o, ix, iy)] += fb[(long)(q * 6 + k) * N + nid(o, tx, ty)];
+                    }
+        }
+        /* edges: f_d(x_b) = D f*_{-d}(x_b) + S_d */
+        for (e = 0; e < 4; ++e) {
+            const orc_edge *E = &o->e[e];
+            const int len = edge_len(o, e);
+            int p;
+            if (E->kind == ORC_PERIODIC) continue;
+            for (p = 0; p < len; ++p) {
+                const long nb = edge_node(o, e, 0, p);
+                double D[6];
+                int kk;
+                if (E->kind == ORC_VELOCITY) {
+                    D[0] = -1; D[1] = -1; D[2] = 1; D[3] = 1; D[4] = 1; D[5] = 1;
+                } else {
+                    D[0] = 1; D[1] = 1; D[2] = -1; D[3] = -1; D[4] = -1; D[5] = -1;
+                }
+                for (kk = 0; kk < 6; ++kk)
+                    fsb[(long)(dout[e] * 6 + kk) * N + nb] += D[kk] * fb[(long)(dmiss[e] * 6 + kk) * N + nb];
+                if (E->kind == ORC_TRACTION) {
+                    /* S_F = F^b / 2 with F^b(U^(step-1) at x_b, mu(x_b)) */
+                    const int a = (e == ORC_LEFT || e == ORC_RIGHT) ? 0 : 1, tc = 1 - a;
+                    const double Na = (e == ORC_LEFT || e == ORC_BOTTOM) ? -1.0 : 1.0;
+                    double val[2], Fb[4], Ct[16], Jn[4], Jt[4], Fbb[4], rhs[2], z[2], Pr[4];
+                    double pb[8], unit[8] = {0};
+                    int i, j;
+                    const double *prm = node_prm(o, nb, pb);
+                    edge_value(o, e, p, (step - 1) * dt + 0.5 * dt, val);
+                    if (boundary_F(o, e, p, val, Fb) != 0) {
+                        rc = -5;
+                        goto done;
+                    }
+                    for (kk = 0; kk < 4; ++kk) Fbb[kk] = 0.5 * fb[(long)(dmiss[e] * 6 + 2 + kk) * N + nb];
+                    orc_tangent(o->law, prm, Fb, Ct);
+                    for (i = 0; i < 2; ++i)
+                        for (j = 0; j < 2; ++j) {
+                            Jn[i * 2 + j] = Na * Ct[(i * 2 + a) * 4 + (j * 2 + a)];
+                            Jt[i * 2 + j] = Na * Ct[(i * 2 + a) * 4 + (j * 2 + tc)];
+                        }
+                    /* z = -Jn^{-T} Fbb_normal */
+                    rhs[0] = -Fbb[0 * 2 + a];
+                    rhs[1] = -Fbb[1 * 2 + a];
+                    solve2t(Jn, rhs, z);
+                    for (j = 0; j < 2; ++j)
+                        Ub[(2 + j * 2 + tc) * N + nb] += Fbb[j * 2 + tc] + z[0] * Jt[0 * 2 + j] + z[1] * Jt[1 * 2 + j];
+                    /* dr/dmu = Na P_ia(F^b; lam_ratio, 1) */
+                    unit[0] = o->lam_ratio;
+                    unit[1] = 1.0;
+                    orc_piola(o->law, unit, Fb, Pr);
+                    g_mu[nb] += z[0] * Na * Pr[0 * 2 + a] + z[1] * Na * Pr[1 * 2 + a];
+                }
+            }
+        }
+        /* collision, node by node */
+        for (m = 0; m < N; ++m) {
+            double pb[8], pp[8] = {0}, pm[8] = {0};
+            const double *prm = node_prm(o, m, pb);
+            const double b1 = bforce(o, 0, m), b2 = bforce(o, 1, m);
+            double complex fc[24], fsc[24];
+            double f[24], sb[24], dmu = 0.0;
+            int i, j;
+            for (j = 0; j < 24; ++j) {
+                f[j] = o->f[(long)j * N + m];
+                sb[j] = fsb[(long)j * N + m];
+            }
+            for (j = 0; j < 24; ++j) {
+                double acc = 0.0;
+                for (i = 0; i < 24; ++i) fc[i] = f[i];
+                fc[j] += 1e-30 * I;
+                collide_c(o, prm, b1, b2, fc, fsc);
+                for (i = 0; i < 24; ++i) acc += (cimag(fsc[i]) / 1e-30) * sb[i];
+                fbn[(long)j * N + m] = acc + Ub[(j % 6) * N + m];
+            }
+            /* d fs / d mu: affine in mu, central difference over +-mu/2 */
+            pp[0] = o->lam_ratio * 1.5 * o->mufield[m];
+            pp[1] = 1.5 * o->mufield[m];
+            pm[0] = o->lam_ratio * 0.5 * o->mufield[m];
+            pm[1] = 0.5 * o->mufield[m];
+            {
+                double complex fp[24], fm[24];
+                for (i = 0; i < 24; ++i) fc[i] = f[i];
+                collide_c(o, pp, b1, b2, fc, fp);
+                collide_c(o, pm, b1, b2, fc, fm);
+                for (i = 0; i < 24; ++i) dmu += (creal(fp[i]) - creal(fm[i])) / o->mufield[m] * sb[i];
+            }
+            g_mu[m] += dmu;
+        }
+        {
+            double *t = fb;
+            fb = fbn;
+            fbn = t;
+        }
+    }
+    /* init: f^0 = init(U0; mu), u*^0 = u0 - (dt/2) v0 */
+    memcpy(mu_save, o->mufield, (size_t)N * sizeof(double));
+    for (m = 0; m < N; ++m) {
+        int cc;
+        for (cc = 0; cc < 2; ++cc) {
+            double acc = 0.0;
+            long j;
+            memcpy(U0p, U0, (size_t)6 * N * sizeof(double));
+            U0p[cc * N + m] = U0[cc * N + m] + 1.0;
+            orc_init(o, U0p, NULL, order, NULL, NULL);
+            memcpy(f0p, o->f, (size_t)24 * N * sizeof(double));
+            U0p[cc * N + m] = U0[cc * N + m] - 1.0;
+            orc_init(o, U0p, NULL, order, NULL, NULL);
+            memcpy(f0m, o->f, (size_t)24 * N * sizeof(double));
+            for (j = 0; j < 24 * N; ++j) acc += 0.5 * (f0p[j] - f0m[j]) * fb[j];
+            g_v0[cc * N + m] = acc - 0.5 * dt * ub[cc * N + m];
+        }
+        {
+            double acc = 0.0;
+            long j;
+            o->mufield[m] = 1.5 * mu_save[m];
+            orc_init(o, U0, NULL, order, NULL, NULL);
+            memcpy(f0p, o->f, (size_t)24 * N * sizeof(double));
+            o->mufield[m] = 0.5 * mu_save[m];
+            orc_init(o, U0, NULL, order, NULL, NULL);
+            memcpy(f0m, o->f, (size_t)24 * N * sizeof(double));
+            o->mufield[m] = mu_save[m];
+            for (j = 0; j < 24 * N; ++j) acc += (f0p[j] - f0m[j]) / mu_save[m] * fb[j];
+            g_mu[m] += acc;
+        }
+    }
+    /* leave the lattice in its final forward state */
+    memcpy(o->f, fh + (size_t)nsteps * 24 * N, (size_t)24 * N * sizeof(double));
+    memcpy(o->ustar, uh + (size_t)nsteps * 2 * N, (size_t)2 * N * sizeof(double));
+    o->step = nsteps;
+done:
+    free(fh);
+    free(uh);
+    free(fb);
+    free(fbn);
+    free(fsb);
+    free(Ub);
+    free(ub);
+    free(U0p);
+    free(f0p);
+    free(f0m);
+    free(mu_save);
+    return rc;
+}

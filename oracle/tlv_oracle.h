@@ -58,6 +58,10 @@ orc   *orc_new(int nx, int ny, double dx, double c, double omega);
 void   orc_free(orc *o);
 int    orc_set_law(orc *o, int law, const double *prm, int nprm);
 int    orc_set_fb_mode(orc *o, int mode);
+/* per-node shear modulus mu_N (N values, > 0) with lambda = lam_ratio * mu for
+ * SVK, NH and LOGNH (set the law first; orc_set_law drops the field); NULL
+ * reverts to the uniform parameters. Copied. */
+int    orc_set_material_field(orc *o, const double *mu_N, double lam_ratio);
 void   orc_set_body_force(orc *o, double b1, double b2);
 /* per-node body acceleration b(X, t^n) for the current time level; NULL
  * reverts to the uniform value. Copied. */
@@ -80,6 +84,17 @@ void   orc_displacement(const orc *o, double *u);
 void   orc_populations(const orc *o, double *f);     /* pre-collision f^n, 24N */
 void   orc_set_populations(orc *o, const double *f);  /* inverse of the above   */
 int    orc_status(const orc *o);
+/* Reference adjoint. Runs orc_init(U0, u0 = 0, order) and nsteps steps and
+ * returns L = 1/2 sum_k sum_s |u(X_s, t^{n_k}) - d_{k,s}|^2 (sensor node
+ * indices sens[nsens], recorded steps rec_steps[nrec] in [0, nsteps], targets
+ * d as target[(k * nsens + s) * 2 + c]) with dL/dmu (N, the shear-modulus
+ * field; lambda = lam_ratio mu) and dL/dv0 (2N, the initial velocity).
+ * Needs a material field and the node form of F^b. Returns 0, or < 0 on bad
+ * arguments (-1), allocation (-2), init (-3), a latched status (-4) or a
+ * Newton failure (-5). Keeps every forward state: small lattices only. */
+int    orc_adjoint(orc *o, const double *U0, int order, int nsteps, int nsens, const long *sens,
+                   int nrec, const int *rec_steps, const double *target, double *loss, double *g_mu,
+                   double *g_v0);
 long   orc_step_count(const orc *o);
 double orc_time(const orc *o);
 double orc_dt(const orc *o);
