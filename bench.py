@@ -4,8 +4,9 @@ Workload (one "step" = one time step of the whole path over the lattice):
 a 4096 x 2048 clamped specimen -- clamped left edge, traction-free top and
 bottom, traction ramp (0.3 mu sin^2) on the right edge, NH lambda = 2, mu = 1,
 body force (0, -1e-6), c = 5, omega = 1.95 -- with FP32 populations and an FP64
-displacement accumulator. Every step runs the edge kernel (velocity and
-traction reconstruction with the Newton solve) and the fused bulk kernel.
+displacement accumulator. Every step is one launch of the fused kernel, which
+also writes the next step's edge ghosts (velocity and traction rules with the
+Newton solve).
 
 Reported (one JSON line on rank 0):
   value     MLUPS with the state resident in HBM, timed with CUDA events on
@@ -16,8 +17,9 @@ Reported (one JSON line on rank 0):
   roofline  the bulk kernel's algorithmic bytes per launch (224 B per node)
             over its mean event-timed launch duration, against the measured
             HBM copy bandwidth;
-  forms     the same step with FP64, BF16 and FP16 population storage, and the
-            8192^2 periodic workload in FP32 and BF16;
+  forms     the same step with FP64, BF16 and FP16 population storage, the
+            8192^2 periodic workload in FP32 and BF16, and 256 specimens of
+            uneven size and material in batched launches (FP32);
   cpu_baseline  the FP64 CPU oracle on a bounded sample (512 x 256 scaled
             specimen) on one host core.
 --impl reference times the oracle alone as the reference arm.
@@ -286,6 +288,8 @@ def run_ours(args, rank, ws, dist):
                 "note": "16-mode random velocity field, NH lambda=1.5 mu=0.75, omega=2"}
         del Up, up
 
+        forms["batch_256_specimens_fp32"] = batch_form(lbm, torch, peak, k)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(seconds=12.0)
@@ -312,6 +316,59 @@ def run_ours(args, rank, ws, dist):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     return line
+
+
+def batch_form(lbm, torch, peak, steps, graph_steps=20):
+    """256 specimens of uneven size and material (FP32) advanced by the
+    batched launches: tuned tiles replayed from a CUDA graph (the value), and
+    beside it the same with direct launches and with the default tiles."""
+    from synth.generators import specimen_batch
+
+    ws = specimen_batch()
+    kinds = {"velocity": lbm.LBM_BC_VELOCITY, "traction": lbm.LBM_BC_TRACTION}
+    Ls = []
+    for w in ws:
+        L = lbm.Lattice(w.nx, w.ny, dx=w.dx, c=w.c, omega=w.omega, storage=lbm.LBM_STORE_F32)
+        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [w.lam, w.mu])
+        for e, E in enumerate(w.edges):
+            lbm.lbm_set_boundary(L.ctx, e, kinds[E.kind], E.value)
+        U0, u0 = w.fields()
+        lbm.lbm_init(L.ctx, U0, u0, 2)
+        Ls.append(L)
+    nodes = sum(w.nx * w.ny for w in ws)
+    bpn = lbm.lbm_bytes_per_node_update(Ls[0].ctx)
+    b = lbm.lbm_batch_create([L.ctx for L in Ls])
+    st = torch.cuda.current_stream()
+
+    def run(gs):
+        lbm.lbm_batch_step(b, 2 * graph_steps, gs)  # warm-up (and capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lbm.lbm_batch_step(b, steps, gs)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    default_tiles = lbm.lbm_batch_get_tiles(b)
+    ms_default = run(graph_steps)
+    tiles, us = lbm.lbm_batch_tune(b, reps=10)
+    ms = run(graph_steps)
+    ms_direct = run(0)
+    info = lbm.lbm_batch_info(b)
+    lbm.lbm_batch_destroy(b)
+    for L in Ls:
+        L.close()
+    gbs = bpn * nodes * steps / (ms * 1e-3) / 1e9
+    return {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps, "kernel_GBs": gbs,
+            "roofline_frac": gbs / peak, "bytes_per_node": bpn, "nodes": nodes,
+            "launches_per_step": info["launches_per_step"], "graph_steps": graph_steps,
+            "tiles": tiles, "default_tiles": default_tiles,
+            "tune_us": [[round(x, 1) for x in row] for row in us.tolist()],
+            "value_direct_launches": nodes * steps / (ms_direct * 1e-3) / 1e6,
+            "value_default_tiles": nodes * steps / (ms_default * 1e-3) / 1e6,
+            "note": "seed-2 specimens, N log-uniform 64^2..1024^2, aspect 1..4, NH mu U(0.2,2), lambda/mu "
+                    "U(1,4), clamped left, other edges clamped or traction-free; GB/s over the whole step"}
 
 
 def oracle_sample(nx=512, ny=256):

@@ -229,6 +229,72 @@ lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t nx, int32_
                                          const double *params, int32_t nparams, double dx, double *out_dev,
                                          int32_t device, void *stream);
 
+/* ------------------------------------------------------------ batches
+ * Many lattices ("members": specimens of uneven size, material and edges)
+ * advanced together by shared persistent launches. The paper has no
+ * counterpart; every member still follows Sec. 3.7 exactly: after
+ * lbm_batch_step(b, n, ...) each member holds, bit for bit, the state that
+ * lbm_step(member, n) would have produced from the same start.
+ *
+ * Members are grouped by closure and size class; each group is one launch
+ * per step over a work list of (member, row, segment) tasks, and the groups of
+ * a step run concurrently. A segment is 32 x vec consecutive nodes of a row
+ * ("tile": vec nodes per lane); vec is chosen per size class of nx:
+ *   class 0: nx <= 48, 1: nx <= 96, 2: nx <= 192, 3: nx <= 384, 4: larger.
+ * Tiles that exist: F64 {1, 2}, F32 {1, 2, 4}, BF16 / F16 {2, 4}. The default
+ * tile of a class is the widest whose segment is no wider than the class's
+ * largest nx (48, 96, 192, 384; the narrowest if none is); lbm_batch_tune
+ * measures them all.
+ *
+ * The batch owns a stream of its own. Every call orders its device work after
+ * the work already enqueued on the members' streams, and the members' streams
+ * after it. */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+#define LBM_BATCH_MAX_MEMBERS 4096
+#define LBM_BATCH_CLASSES 5
+
+/* members: host array of n distinct contexts (1 <= n <= LBM_BATCH_MAX_MEMBERS)
+ * created on one device with one storage type and fb_mode LBM_FB_NODE
+ * (LBM_ERR_ARG otherwise). The contexts stay owned by the caller, must outlive
+ * the batch and can still be used on their own between batch calls. Errors
+ * of create are reported by lbm_batch_last_error(NULL). */
+lbm_status lbm_batch_create(lbm_ctx *const *members, int32_t n, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* size class of a lattice of width nx (0 .. LBM_BATCH_CLASSES - 1) */
+int32_t lbm_batch_size_class(int32_t nx);
+
+/* Tiles (nodes per lane) of the size classes: vec[LBM_BATCH_CLASSES] (host).
+ * lbm_batch_set_tile returns LBM_ERR_ARG for a tile that does not exist for
+ * the members' storage. */
+lbm_status lbm_batch_get_tiles(const lbm_batch *b, int32_t *vec);
+lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t size_class, int32_t vec);
+
+/* Autotuner: for every size class that has members, times `reps` (>= 1)
+ * launches of that class alone for each tile that exists and keeps the
+ * fastest. The trial launches write only the members' second population
+ * buffer and scratch copies of the displacement accumulator and status, so
+ * the members' states do not change. us (host, optional) receives
+ * LBM_BATCH_CLASSES x 3 doubles: mean microseconds per launch for the tiles
+ * in the order listed above (0 where not tried). Synchronises. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us);
+
+/* Advance every member by nsteps >= 0 steps. graph_steps = 0 enqueues the
+ * launches one by one; an even graph_steps >= 2 captures the launches of
+ * graph_steps steps once into a CUDA graph (captured again when the tiles or
+ * the members' closures change) and replays it, enqueueing the remainder
+ * directly. Every member must be initialised (LBM_ERR_STATE). member_status
+ * (host, optional, n) receives each member's status. Synchronises; returns
+ * LBM_OK or the status of the first member that failed (whose own
+ * lbm_last_error explains it). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps, int32_t graph_steps, int32_t *member_status);
+
+/* Total nodes of the members, kernel launches per step and graphs captured
+ * so far (any may be NULL). No device work. */
+lbm_status lbm_batch_info(const lbm_batch *b, int64_t *nodes, int32_t *launches_per_step, int32_t *graphs);
+
 #ifdef __cplusplus
 }
 #endif

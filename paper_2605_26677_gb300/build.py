@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUTDIR, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_aux.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_batch_k32.cu",
+           "lbm_batch_k16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -10,36 +10,10 @@
 #include <string>
 #include <vector>
 
-#include "lbm.h"
 #include "lbm_internal.h"
 
 using namespace tlv;
 
-struct lbm_ctx {
-    lbm_config cfg{};
-    cudaStream_t st = nullptr;
-    int eb = 4;            // bytes per stored population value
-    Layout L{};
-    void *f[2] = {nullptr, nullptr};
-    double *ustar = nullptr;
-    int *d_status = nullptr;
-    double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
-    double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
-    int cur = 0;
-    long long step = 0;
-    double dt = 0.0;
-    Material m{};
-    bool have_material = false;
-    double b[2] = {0.0, 0.0};
-    EdgeDesc edge[4]{};
-    bool initialized = false;
-    bool ghosts_dirty = true;  // ghost cells of f[cur] must be rebuilt before the next step
-    int grid_step = 1;
-    int edge_blk_end[4] = {0, 0, 0, 0};
-    std::string err;
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_step, ev_edge; // start/stop pairs
-};
 
 static thread_local std::string g_create_err;
 
@@ -106,6 +80,20 @@ lbm_status sync_status(lbm_ctx *c)
     return map_flags(c, flags);
 }
 
+} // namespace
+
+// The step that starts from f*^n (n = step) computes f*^{n+1} and writes the
+// ghosts the next step pulls, whose edge data belong to t^{n+1} + dt/2
+// (Eq. 23). One out-of-line function serves the single and batched paths so
+// that both see the same rounding.
+__attribute__((noinline)) double tlv::ctx_time_factor(const lbm_ctx *c, int e, long long step)
+{
+    const double th = ((double)step + 1.5) * c->dt;
+    return timefn(c->edge[e].timefn, c->edge[e].tp, th);
+}
+
+namespace {
+
 template <typename T>
 StepArgs<T> step_args(const lbm_ctx *c, int cur)
 {
@@ -128,16 +116,14 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.mu = (T)c->m.mu;
     a.c = (T)c->cfg.c;
     a.dt = c->dt;
-    // this launch computes f*^{n+1} (n = c->step) and writes the ghosts the
-    // next step pulls, whose edge data belong to t^{n+1} + dt/2 (Eq. 23)
-    const double th = ((double)c->step + 1.5) * c->dt;
     for (int e = 0; e < 4; ++e) {
         a.kind[e] = c->edge[e].kind;
         a.value[e][0] = c->edge[e].value[0];
         a.value[e][1] = c->edge[e].value[1];
-        a.g[e] = timefn(c->edge[e].timefn, c->edge[e].tp, th);
+        a.g[e] = ctx_time_factor(c, e, c->step);
         a.profile[e] = c->edge[e].profile;
     }
+    a.gdev = nullptr;
     return a;
 }
 
@@ -312,6 +298,30 @@ lbm_status refresh_ghosts(lbm_ctx *c)
 }
 
 } // namespace
+
+namespace tlv {
+
+lbm_status ctx_fail(lbm_ctx *c, lbm_status s, const std::string &msg) { return fail(c, s, msg); }
+
+lbm_status ctx_map_flags(lbm_ctx *c, int flags) { return map_flags(c, flags); }
+
+lbm_status ctx_ready(lbm_ctx *c)
+{
+    lbm_status s = check_ready(c);
+    return s != LBM_OK ? s : check_edges(c);
+}
+
+lbm_status ctx_refresh_ghosts(lbm_ctx *c) { return refresh_ghosts<double>(c); }
+
+template <typename T>
+StepArgs<T> ctx_step_args(const lbm_ctx *c, int cur)
+{
+    return step_args<T>(c, cur);
+}
+template StepArgs<float> ctx_step_args<float>(const lbm_ctx *, int);
+template StepArgs<double> ctx_step_args<double>(const lbm_ctx *, int);
+
+} // namespace tlv
 
 // ====================================================================== ABI
 

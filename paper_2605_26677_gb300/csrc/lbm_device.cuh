@@ -7,9 +7,10 @@
 // column xoff + nx are ghost columns (x = -1, x = nx). Node (x, y) lives at
 //   p * plane + (y + 1) * pitch + xoff + x.
 // xoff is 128 bytes, so every row of real nodes starts on a 128-byte line.
-// The edge kernel writes, before each step, the value each boundary node
-// pulls from outside the domain into the ghost cell it pulls from; the bulk
-// kernel is then a uniform pull over all nodes.
+// Before each step the ghost cells hold the value each boundary node pulls
+// from outside the domain (written by the previous step's fused kernel, or by
+// the ghost or edge kernel), so the bulk kernel is a uniform pull over all
+// nodes.
 //
 // Stored values are offsets from the rest equilibrium f_rest =
 // (0, 0, 1/4, 0, 0, 1/4) (Eq. 12 at F = I, v = 0, where P(I) = 0), so the sum
@@ -119,7 +120,28 @@ struct StepArgs {
     // value * g * profile[s], g = g(t^n + dt/2) evaluated once on the host
     int kind[4];
     double value[4][2], g[4];
+    const double *gdev;          // if set, the time factors are read here instead of g
     const double *profile[4];
+};
+
+// A batch of lattices for one persistent launch
+constexpr int BATCH_MAX_MEMBERS = 4096;
+struct BatchList {
+    const void *args;  // StepArgs<R>[n]
+    const int *off;    // n + 1 prefix sums of the members' task counts
+    int n;
+};
+
+// Edge time factors of a batch: the host tabulates g(t) of every member's
+// edges for the steps of one call (the same function and arguments as the
+// single-lattice path), and before each step a one-block kernel copies row k
+// of the table to the slot the members' StepArgs::gdev point at.
+struct BatchTime {
+    const double *tab;  // [K][n4]
+    int *k;             // next row
+    double *g;          // [n4]
+    int n4;
+    int rows;           // K
 };
 
 struct EdgeArgs {

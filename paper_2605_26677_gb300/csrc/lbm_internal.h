@@ -2,10 +2,40 @@
 // translation units (kernel launchers); not part of the public C ABI.
 #pragma once
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
+#include "lbm.h"
 #include "lbm_device.cuh"
+
+// One lattice: the object behind the opaque lbm_ctx handle of the C ABI.
+struct lbm_ctx {
+    lbm_config cfg{};
+    cudaStream_t st = nullptr;
+    int eb = 4;            // bytes per stored population value
+    tlv::Layout L{};
+    void *f[2] = {nullptr, nullptr};
+    double *ustar = nullptr;
+    int *d_status = nullptr;
+    double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
+    double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
+    int cur = 0;
+    long long step = 0;
+    double dt = 0.0;
+    tlv::Material m{};
+    bool have_material = false;
+    double b[2] = {0.0, 0.0};
+    tlv::EdgeDesc edge[4]{};
+    bool initialized = false;
+    bool ghosts_dirty = true;  // ghost cells of f[cur] must be rebuilt before the next step
+    int grid_step = 1;
+    int edge_blk_end[4] = {0, 0, 0, 0};
+    std::string err;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_step, ev_edge; // start/stop pairs
+};
+
 
 namespace tlv {
 
@@ -60,5 +90,19 @@ cudaError_t launch_diag(int storage, const DiagArgs &a, cudaStream_t st);
 
 // lbm_api.cu: message returned by lbm_last_error(NULL) on this host thread
 void set_thread_error(const std::string &msg);
+
+// lbm_api.cu: context operations shared with the batch entry points
+lbm_status ctx_fail(lbm_ctx *c, lbm_status s, const std::string &msg);
+lbm_status ctx_map_flags(lbm_ctx *c, int flags);  // device status bits -> status (and message)
+lbm_status ctx_ready(lbm_ctx *c);                 // initialized, edges consistent, device current
+lbm_status ctx_refresh_ghosts(lbm_ctx *c);        // rebuild stale ghost cells (stream-ordered)
+template <typename T>
+StepArgs<T> ctx_step_args(const lbm_ctx *c, int cur);  // arguments of the step that reads f[cur]
+double ctx_time_factor(const lbm_ctx *c, int e, long long step);  // g of edge e for the step from f*^step
+
+// lbm_batch_k32.cu / lbm_batch_k16.cu: batched step kernel for (law, nodes
+// per lane), or nullptr if that form is not built
+const void *batch_kernel_wide(int storage, int law, int vec);
+const void *batch_kernel_16(int storage, int law, int vec);
 
 } // namespace tlv

@@ -30,7 +30,11 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "l
            "lbm_set_boundary", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
            "lbm_read_state", "lbm_read_state_device", "lbm_read_displacement", "lbm_read_displacement_device",
            "lbm_read_cauchy", "lbm_diagnostics", "lbm_save", "lbm_load", "lbm_info", "lbm_profile",
-           "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc"]
+           "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc",
+           "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_size_class",
+           "lbm_batch_get_tiles", "lbm_batch_set_tile", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_info"]
+LBM_BATCH_MAX_MEMBERS = 4096
+LBM_BATCH_CLASSES = 5
 
 
 class lbm_config(C.Structure):
@@ -90,6 +94,21 @@ _lib.lbm_bytes_per_node_update.argtypes = [_ctx]
 _lib.lbm_bytes_per_node_update.restype = C.c_double
 _lib.lbm_diagnostics_state_noalloc.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int32,
                                                C.c_double, C.c_void_p, C.c_int32, C.c_void_p]
+
+
+_ip = C.POINTER(C.c_int32)
+_lib.lbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
+_lib.lbm_batch_destroy.argtypes = [C.c_void_p]
+_lib.lbm_batch_destroy.restype = None
+_lib.lbm_batch_last_error.argtypes = [C.c_void_p]
+_lib.lbm_batch_last_error.restype = C.c_char_p
+_lib.lbm_batch_size_class.argtypes = [C.c_int32]
+_lib.lbm_batch_size_class.restype = C.c_int32
+_lib.lbm_batch_get_tiles.argtypes = [C.c_void_p, _ip]
+_lib.lbm_batch_set_tile.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+_lib.lbm_batch_tune.argtypes = [C.c_void_p, C.c_int32, _dp]
+_lib.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _ip]
+_lib.lbm_batch_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _ip, _ip]
 
 
 def library():
@@ -304,6 +323,78 @@ def lbm_diagnostics_state_noalloc(U_dev, nx, ny, law, params, dx, out_dev, devic
     st = _lib.lbm_diagnostics_state_noalloc(_dev(U_dev, 6 * nx * ny), nx, ny, law, p.ctypes.data_as(_dp), len(p),
                                             dx, _dev(out_dev, 10), device, C.c_void_p(stream or None))
     _check(None, st)
+
+
+# ---------------------------------------------------------------- batches
+class Batch:
+    """Opaque batch handle returned by lbm_batch_create; keeps its members
+    (Context objects) referenced."""
+
+    def __init__(self, handle, members):
+        self._as_parameter_ = handle
+        self.members = list(members)
+
+
+def _bcheck(b, status):
+    if status != LBM_OK:
+        msg = _lib.lbm_batch_last_error(b)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+def lbm_batch_create(members):
+    """members: sequence of contexts (lbm_create handles)."""
+    arr = (C.c_void_p * len(members))(*[m._as_parameter_ for m in members])
+    h = C.c_void_p()
+    _bcheck(None, _lib.lbm_batch_create(arr, len(members), C.byref(h)))
+    return Batch(h, members)
+
+
+def lbm_batch_destroy(b):
+    if b is not None and b._as_parameter_ is not None:
+        _lib.lbm_batch_destroy(b)
+        b._as_parameter_ = None
+
+
+def lbm_batch_last_error(b=None):
+    m = _lib.lbm_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def lbm_batch_size_class(nx):
+    return _lib.lbm_batch_size_class(int(nx))
+
+
+def lbm_batch_get_tiles(b):
+    v = (C.c_int32 * LBM_BATCH_CLASSES)()
+    _bcheck(b, _lib.lbm_batch_get_tiles(b, v))
+    return list(v)
+
+
+def lbm_batch_set_tile(b, size_class, vec):
+    _bcheck(b, _lib.lbm_batch_set_tile(b, int(size_class), int(vec)))
+
+
+def lbm_batch_tune(b, reps=20):
+    """Returns (tiles per class, microseconds per launch [class][tile index])."""
+    us = np.zeros(LBM_BATCH_CLASSES * 3)
+    _bcheck(b, _lib.lbm_batch_tune(b, int(reps), us.ctypes.data_as(_dp)))
+    return lbm_batch_get_tiles(b), us.reshape(LBM_BATCH_CLASSES, 3)
+
+
+def lbm_batch_step(b, nsteps, graph_steps=0, raise_on_error=True):
+    """Returns the per-member status list."""
+    st = (C.c_int32 * len(b.members))()
+    s = _lib.lbm_batch_step(b, int(nsteps), int(graph_steps), st)
+    if raise_on_error:
+        _bcheck(b, s)
+    return list(st)
+
+
+def lbm_batch_info(b):
+    n, l, g = C.c_int64(), C.c_int32(), C.c_int32()
+    _bcheck(b, _lib.lbm_batch_info(b, C.byref(n), C.byref(l), C.byref(g)))
+    return {"nodes": n.value, "launches_per_step": l.value, "graphs": g.value}
 
 
 # ---------------------------------------------------------------- helper

@@ -14,7 +14,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["splitmix64_uniform", "Workload", "shear_wave_64", "clamped_specimen",
-           "fourier_periodic", "rest_state", "WORKLOADS"]
+           "fourier_periodic", "specimen_batch", "rest_state", "WORKLOADS"]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -57,6 +57,7 @@ class Workload:
     edges: list = field(default_factory=lambda: [Edge(), Edge(), Edge(), Edge()])
     seed: int = 0
     note: str = ""
+    params: dict = field(default_factory=dict)  # workload-specific draws
 
     def fields(self):
         """(U0, u0) initial state and displacement, float64 (6|2, ny, nx)."""
@@ -156,7 +157,57 @@ def fourier_periodic(n=8192, storage="f32", steps=5000, seed=1):
                     storage=storage, seed=seed, note="periodic square, 16-mode random velocity")
 
 
+def _batch_member_fields(w: Workload):
+    """v = 0.02 (cos th, sin th) sin(pi X / Lx) sin(pi Y / Ly) with X, Y the node
+    coordinates (ix + 1/2, iy + 1/2) dx and Lx = nx dx, Ly = ny dx; F = I."""
+    nx, ny = w.nx, w.ny
+    th = w.params["theta"]
+    U0 = rest_state(nx, ny)
+    sx = np.sin(np.pi * (np.arange(nx) + 0.5) / nx)
+    sy = np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+    prof = 0.02 * sy[:, None] * sx[None, :]
+    U0[0] = np.cos(th) * prof
+    U0[1] = np.sin(th) * prof
+    return U0, np.zeros((2, ny, nx))
+
+
+def specimen_batch(n=256, seed=2, side_min=64, side_max=1024, storage="f32", steps=2000, omega=1.95,
+                   aspect_max=4.0):
+    """n specimens of uneven size and material. Eight draws per specimen from
+    the seeded stream (specimen k uses draws 8k .. 8k+7):
+      node count N log-uniform in [side_min^2, side_max^2], aspect ratio
+      A = nx / ny uniform in [1, aspect_max], nx = round(sqrt(N A)), ny = round(sqrt(N / A))
+      (at least 3 each); mu uniform in [0.2, 2]; lambda / mu uniform in [1, 4];
+      right, bottom and top edges each clamped (velocity 0) or traction-free
+      with probability 1/2; the initial velocity direction theta uniform in
+      [0, 2 pi). The left edge is clamped. NH closure, c = max(5, 3 c_P) with
+      c_P = sqrt(lambda + 2 mu) (rho_0 = 1), omega = 1.95, no body force.
+      With c = 2 c_P some members (e.g. member 128 of the seed-2 draw, lambda /
+      mu = 3.9, clamped left and top, traction-free right and bottom) grow
+      without bound after about 1000 steps in the FP64 oracle; 2.5 c_P and
+      3 c_P keep it bounded over 2000 steps."""
+    r = splitmix64_uniform(seed, 8 * n).reshape(n, 8)
+    lo, hi = 2.0 * np.log(side_min), 2.0 * np.log(side_max)
+    out = []
+    for k in range(n):
+        a = r[k]
+        N = np.exp(lo + a[0] * (hi - lo))
+        A = 1.0 + (aspect_max - 1.0) * a[1]
+        nx = max(3, int(round(np.sqrt(N * A))))
+        ny = max(3, int(round(np.sqrt(N / A))))
+        mu = 0.2 + 1.8 * a[2]
+        lam = mu * (1.0 + 3.0 * a[3])
+        c = max(5.0, 3.0 * np.sqrt(lam + 2.0 * mu))
+        kinds = ["velocity" if a[4 + j] < 0.5 else "traction" for j in range(3)]
+        edges = [Edge("velocity")] + [Edge(kd) for kd in kinds]
+        out.append(Workload("batch_member", nx, ny, lam=lam, mu=mu, c=c, omega=omega, steps=steps,
+                            storage=storage, edges=edges, seed=seed, params={"theta": 2.0 * np.pi * a[7]},
+                            note="member %d of a specimen batch" % k))
+    return out
+
+
 _FIELD_BUILDERS["shear_wave"] = _shear_wave_fields
+_FIELD_BUILDERS["batch_member"] = _batch_member_fields
 _FIELD_BUILDERS["clamped_specimen"] = _rest_fields
 _FIELD_BUILDERS["fourier_periodic"] = _fourier_fields
 
@@ -164,4 +215,5 @@ WORKLOADS = {
     "shear_wave_64": shear_wave_64,
     "clamped_specimen": clamped_specimen,
     "fourier_periodic": fourier_periodic,
+    "specimen_batch": specimen_batch,
 }

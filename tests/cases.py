@@ -31,6 +31,18 @@ class Case:
     u0: np.ndarray = None
 
 
+def case_from_workload(w, steps=None):
+    """A Case with the sizes, material, edges and initial fields of a
+    synthetic Workload (NH closure)."""
+    U0, u0 = w.fields()
+    edges = {}
+    for e, E in enumerate(w.edges):
+        if E.kind != "periodic":
+            edges[e] = (E.kind, E.value, E.timefn, E.tparams, E.profile)
+    return Case(w.nx, w.ny, w.steps if steps is None else steps, lam=w.lam, mu=w.mu, c=w.c, omega=w.omega,
+                dx=w.dx, body=w.body_force, edges=edges, U0=U0, u0=u0)
+
+
 def smooth_field(nx, ny, seed, amp=0.02, modes=3, periodic=True):
     """Smooth initial state around F = I, v = 0 from a seeded stream."""
     from synth import splitmix64_uniform

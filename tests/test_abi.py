@@ -62,3 +62,25 @@ def test_create_rejects_bad_configs_before_touching_the_device(lbm, kw, err):
         lbm.lbm_create(**kw)
     assert str(ei.value).startswith(err)
     assert lbm.lbm_last_error(None)
+
+
+def test_batch_size_classes(lbm):
+    # class k holds widths up to 48, 96, 192, 384 and beyond
+    for nx, k in ((1, 0), (48, 0), (49, 1), (96, 1), (97, 2), (192, 2), (193, 3), (384, 3), (385, 4),
+                  (1 << 24, 4)):
+        assert lbm.lbm_batch_size_class(nx) == k
+
+
+def test_batch_create_rejects_bad_arguments_before_touching_the_device(lbm):
+    import ctypes as C
+
+    lib = lbm.library()
+    out = C.c_void_p()
+    assert lib.lbm_batch_create(None, 1, C.byref(out)) == lbm.LBM_ERR_ARG
+    arr = (C.c_void_p * 1)(None)
+    assert lib.lbm_batch_create(arr, 1, C.byref(out)) == lbm.LBM_ERR_ARG
+    assert b"NULL" in lib.lbm_batch_last_error(None)
+    assert lib.lbm_batch_create(arr, 0, C.byref(out)) == lbm.LBM_ERR_ARG
+    assert lib.lbm_batch_create(arr, lbm.LBM_BATCH_MAX_MEMBERS + 1, C.byref(out)) == lbm.LBM_ERR_ARG
+    assert out.value is None
+    assert lib.lbm_batch_step(None, 1, 0, None) == lbm.LBM_ERR_ARG

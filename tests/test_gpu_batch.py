@@ -1,0 +1,286 @@
+"""Batched launches (many specimens of uneven size, material and edges in one
+persistent launch per group, optionally replayed from a CUDA graph) through
+the C ABI.
+
+Every member of a batch follows the single-lattice step exactly, so the
+checks are: bit-for-bit equality with the same members stepped one context
+at a time (every storage, every tile, graph and direct, odd step counts that
+leave the buffers swapped); FP64 parity of every member with the FP64 oracle;
+the full 256-specimen workload (FP32, tuned tiles, graph) with its smallest
+members against the oracle; per-member status; tuning that leaves the states
+untouched; argument errors."""
+import numpy as np
+import pytest
+
+from tests.cases import case_from_workload, group_errors, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+TILES = {F64: [1, 2], F32: [1, 2, 4], BF16: [2, 4], F16: [2, 4]}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2605_26677_gb300 import build
+
+    build.build()
+    from paper_2605_26677_gb300 import lbm as m
+
+    return m
+
+
+def mixed_members():
+    """Sixteen small specimens across size classes 0-4: twelve from the batch
+    recipe at sides 8-40, four wide ones (nx up to ~380); member 3 carries a
+    sin^2-ramped traction on its right edge, member 5 the SVK closure."""
+    from synth.generators import specimen_batch
+
+    ws = specimen_batch(n=12, seed=2, side_min=8, side_max=40) + \
+        specimen_batch(n=4, seed=7, side_min=40, side_max=60, aspect_max=40.0)
+    from synth.generators import Edge
+
+    ws[3].edges[1] = Edge("traction", (0.05 * ws[3].mu, 0.01), "sin2_ramp", (40 * (1.0 / ws[3].c), 0, 0, 0))
+    cases = [case_from_workload(w, steps=0) for w in ws]
+    cases[5].law = "SVK"
+    return cases
+
+
+def make_ctx(lbm, case, storage):
+    from tests.cases import KIND, LAW_IDS, TIMEFN
+
+    L = lbm.Lattice(case.nx, case.ny, dx=case.dx, c=case.c, omega=case.omega, storage=storage)
+    lbm.lbm_set_material(L.ctx, LAW_IDS[case.law][0], [case.lam, case.mu])
+    lbm.lbm_set_body_force(L.ctx, *case.body)
+    for e, (kind, val, tf, tp, prof) in case.edges.items():
+        lbm.lbm_set_boundary(L.ctx, e, KIND[kind], val, TIMEFN[tf], tp, prof)
+    lbm.lbm_init(L.ctx, case.U0, case.u0, case.order)
+    return L
+
+
+def states(lbm, Ls):
+    out = []
+    for L in Ls:
+        U, _, t = lbm.lbm_read_state(L.ctx, want_P=False)
+        out.append((U, lbm.lbm_read_displacement(L.ctx), t))
+    return out
+
+
+def same(a, b):
+    for (U1, u1, t1), (U2, u2, t2) in zip(a, b):
+        assert t1 == t2
+        assert np.array_equal(U1, U2)
+        assert np.array_equal(u1, u2)
+
+
+def individual(lbm, cases, storage, steps):
+    Ls = [make_ctx(lbm, c, storage) for c in cases]
+    for L in Ls:
+        lbm.lbm_step(L.ctx, steps)
+    s = states(lbm, Ls)
+    for L in Ls:
+        L.close()
+    return s
+
+
+def batched(lbm, cases, storage, steps, graph_steps=0, tile=None, calls=1):
+    Ls = [make_ctx(lbm, c, storage) for c in cases]
+    b = lbm.lbm_batch_create([L.ctx for L in Ls])
+    try:
+        if tile is not None:
+            for k in range(lbm.LBM_BATCH_CLASSES):
+                lbm.lbm_batch_set_tile(b, k, tile)
+        for i in range(calls):
+            st = lbm.lbm_batch_step(b, steps, graph_steps)
+            assert all(s == 0 for s in st)
+        info = lbm.lbm_batch_info(b)
+        s = states(lbm, Ls)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        for L in Ls:
+            L.close()
+    return s, info
+
+
+@pytest.mark.parametrize("storage", [F64, F32, BF16, F16])
+def test_batch_equals_individual(lbm, storage):
+    cases = mixed_members()
+    ref = individual(lbm, cases, storage, 101)
+    got, info = batched(lbm, cases, storage, 101)
+    same(got, ref)
+    assert info["nodes"] == sum(c.nx * c.ny for c in cases)
+    assert info["launches_per_step"] >= 3  # two closures x several tiles + the time-factor kernel
+
+
+@pytest.mark.parametrize("storage", [F64, F32, BF16, F16])
+def test_every_tile_equals_individual(lbm, storage):
+    cases = mixed_members()
+    ref = individual(lbm, cases, storage, 37)
+    for tile in TILES[storage]:
+        got, _ = batched(lbm, cases, storage, 37, tile=tile)
+        same(got, ref)
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_graph_replay_equals_direct(lbm, storage):
+    cases = mixed_members()
+    direct, _ = batched(lbm, cases, storage, 101, graph_steps=0, calls=2)
+    graph, info = batched(lbm, cases, storage, 101, graph_steps=8, calls=2)
+    same(graph, direct)
+    assert info["graphs"] == 1  # captured once, replayed by both calls
+
+
+def test_long_time_table_chunks(lbm):
+    # 2500 steps cross two refills of the 1024-step edge time table
+    cases = mixed_members()[:4]
+    ref = individual(lbm, cases, F32, 2500)
+    got, _ = batched(lbm, cases, F32, 2500, graph_steps=16)
+    same(got, ref)
+
+
+def test_batch_fp64_matches_oracle(lbm):
+    from tests.test_gpu_parity import TOL
+
+    cases = mixed_members()
+    got, _ = batched(lbm, cases, F64, 200, graph_steps=10)
+    for c, (U, u, t) in zip(cases, got):
+        c.steps = 200
+        o = run_oracle(c)
+        P = o["P"]  # the group errors need a GPU P: compare U and u only
+        g = {"U": U, "P": P, "u": u, "sigma": o["sigma"]}
+        errs = group_errors(g, o)
+        for k in ("v", "F-I", "u"):
+            assert errs[k] <= TOL[F64]["group"], (c.nx, c.ny, k, errs)
+        assert errs["U"] <= TOL[F64]["U"], (c.nx, c.ny, errs)
+        assert abs(t - o["t"]) < 1e-12
+
+
+def test_tuning_keeps_states(lbm):
+    cases = mixed_members()
+    Ls = [make_ctx(lbm, c, F32) for c in cases]
+    b = lbm.lbm_batch_create([L.ctx for L in Ls])
+    try:
+        lbm.lbm_batch_step(b, 7)
+        before = states(lbm, Ls)
+        tiles, us = lbm.lbm_batch_tune(b, reps=5)
+        for k, v in enumerate(tiles):
+            assert v in TILES[F32]
+        present = {lbm.lbm_batch_size_class(c.nx) for c in cases}
+        for k in range(lbm.LBM_BATCH_CLASSES):
+            assert (us[k] > 0).all() == (k in present)
+        same(states(lbm, Ls), before)
+        lbm.lbm_batch_step(b, 30, graph_steps=10)
+        after = states(lbm, Ls)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        for L in Ls:
+            L.close()
+    same(after, individual(lbm, cases, F32, 37))
+
+
+def test_member_status_is_per_member(lbm):
+    from synth.generators import rest_state
+
+    cases = mixed_members()[:5]
+    Ls = [make_ctx(lbm, c, F32) for c in cases]
+    U0 = rest_state(cases[2].nx, cases[2].ny)
+    U0[0, 1, 1] = np.nan
+    lbm.lbm_init(Ls[2].ctx, U0, order=0)
+    b = lbm.lbm_batch_create([L.ctx for L in Ls])
+    try:
+        st = lbm.lbm_batch_step(b, 3, raise_on_error=False)
+        assert st[2] == lbm.LBM_ERR_NONFINITE
+        assert all(s == 0 for i, s in enumerate(st) if i != 2)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_NONFINITE"):
+            lbm.lbm_batch_step(b, 1)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_NONFINITE"):
+            lbm.lbm_sync(Ls[2].ctx)
+        lbm.lbm_sync(Ls[0].ctx)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        for L in Ls:
+            L.close()
+
+
+def test_batch_argument_errors(lbm):
+    cases = mixed_members()[:2]
+    a = make_ctx(lbm, cases[0], F32)
+    b64 = make_ctx(lbm, cases[1], F64)
+    ex = lbm.Lattice(16, 8, storage=F32, fb_mode=lbm.LBM_FB_EXTRAP2)
+    fresh = lbm.Lattice(16, 8, storage=F32)
+    lbm.lbm_set_material(fresh.ctx, lbm.LBM_LAW_NH, [1.0, 0.5])
+    try:
+        for members, what in (([a.ctx, b64.ctx], "storage"), ([a.ctx, a.ctx], "twice"), ([ex.ctx], "node form")):
+            with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+                lbm.lbm_batch_create(members)
+            assert what in lbm.lbm_batch_last_error(None)
+        b = lbm.lbm_batch_create([a.ctx, fresh.ctx])
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+            lbm.lbm_batch_step(b, 1)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_step(b, 1, graph_steps=3)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_step(b, -1)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_set_tile(b, 0, 3)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_set_tile(b, 5, 1)
+        lbm.lbm_batch_destroy(b)
+    finally:
+        for L in (a, b64, ex, fresh):
+            L.close()
+
+
+# ---------------------------------------------------------------- full size
+def test_specimen_batch_256_full_size(lbm):
+    """The 256-specimen workload (FP32, 2000 steps, tuned tiles, graph of 20
+    steps): every member's status is OK and its state finite, and the three
+    smallest members match the FP64 oracle.
+
+    Bounds: the full state U (the paper's norm) to 1e-5. Per group, the FP32
+    traction Newton stops at a relative residual of 4e-6 (against about 6e-8
+    for one FP32 rounding), so each step can inject a relative error of that
+    size at the edges; accumulated as a random walk over n steps and given a
+    factor five, the group bound is 5 * 4e-6 * sqrt(n) (8.9e-4 at n = 2000)."""
+    import torch
+    from synth.generators import specimen_batch
+    from tests.cases import KIND, LAW_IDS
+    from tests.test_gpu_parity import TOL
+
+    ws = specimen_batch()
+    Ls = []
+    try:
+        for w in ws:
+            L = lbm.Lattice(w.nx, w.ny, dx=w.dx, c=w.c, omega=w.omega, storage=F32)
+            lbm.lbm_set_material(L.ctx, LAW_IDS["NH"][0], [w.lam, w.mu])
+            for e, E in enumerate(w.edges):
+                lbm.lbm_set_boundary(L.ctx, e, KIND[E.kind], E.value)
+            U0, u0 = w.fields()
+            lbm.lbm_init(L.ctx, U0, u0)
+            Ls.append(L)
+        b = lbm.lbm_batch_create([L.ctx for L in Ls])
+        lbm.lbm_batch_tune(b, reps=3)
+        st = lbm.lbm_batch_step(b, 2000, graph_steps=20)
+        assert all(s == 0 for s in st)
+        lbm.lbm_batch_destroy(b)
+        order = np.argsort([w.nx * w.ny for w in ws])
+        for k in order[:3]:
+            w = ws[k]
+            U, _, t = lbm.lbm_read_state(Ls[k].ctx, want_P=False)
+            u = lbm.lbm_read_displacement(Ls[k].ctx)
+            o = run_oracle(case_from_workload(w, steps=2000))
+            errs = group_errors({"U": U, "P": o["P"], "u": u, "sigma": o["sigma"]}, o)
+            for g in ("v", "F-I", "u"):
+                assert errs[g] <= 5 * 4e-6 * 2000 ** 0.5, (k, g, errs)
+            assert errs["U"] <= TOL[F32]["U"], (k, errs)
+            print("member", k, w.nx, w.ny, {g: "%.2e" % v for g, v in errs.items()})
+        for k in order[-3:]:
+            U, _, _ = lbm.lbm_read_state(Ls[k].ctx, want_P=False)
+            assert np.isfinite(U).all()
+    finally:
+        for L in Ls:
+            L.close()
+        torch.cuda.synchronize()
