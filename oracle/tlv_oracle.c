@@ -487,13 +487,71 @@ static int check_edges(const orc *o)
     return 0;
 }
 
-/* Sec. 3.4, Eqs. (16)-(21): f_q(X,0) = f^eq(U0) - (dt/2) D_q f^eq(U0) */
+/* Sec. 3.4, Eqs. (16)-(21): f_q(X,0) = f^eq(U0) - (dt/2) D_q f^eq(U0) at node
+ * (ix, iy), with the node's material; f[q*6+k]. Returns ORC_BAD_J or 0. */
+static int init_at(const orc *o, const double *U0, int order, const double *dUdX, const double *dUdY, int ix,
+                   int iy, double f[24])
+{
+    const long N = o->N, n = nid(o, ix, iy);
+    const double c = o->c, dt = o->dt;
+    double U[6], F[4], P[4], pb[8];
+    const double *prm = node_prm(o, n, pb);
+    int q, k, m, mm, st = 0;
+    for (k = 0; k < 6; ++k) U[k] = U0[k * N + n];
+    for (m = 0; m < 4; ++m) F[m] = U[2 + m];
+    if (orc_piola(o->law, prm, F, P) != 0) st = ORC_BAD_J;
+    orc_feq(U, P, c, f);
+    if (order == 2) {
+        double gX[6], gY[6], Ct[16], dPX[4], dPY[4];
+        const double b1 = bforce(o, 0, n), b2 = bforce(o, 1, n);
+        for (k = 0; k < 6; ++k) {
+            gX[k] = dUdX ? dUdX[k * N + n] : fd(o, U0 + k * N, ix, iy, 0);
+            gY[k] = dUdY ? dUdY[k * N + n] : fd(o, U0 + k * N, ix, iy, 1);
+        }
+        orc_tangent(o->law, prm, F, Ct);
+        /* d_alpha P_iA = C_iAkB d_alpha F_kB (text after Eq. 18) */
+        for (m = 0; m < 4; ++m) {
+            dPX[m] = 0.0;
+            dPY[m] = 0.0;
+            for (mm = 0; mm < 4; ++mm) {
+                dPX[m] += Ct[m * 4 + mm] * gX[2 + mm];
+                dPY[m] += Ct[m * 4 + mm] * gY[2 + mm];
+            }
+        }
+        for (q = 0; q < 4; ++q) {
+            const double i = CI[q], j = CJ[q];
+            double Z[6], dP[4], D[6];
+            /* Eq. (18) */
+            Z[0] = b1 + dPX[0] + dPY[1] + c * i * gX[0] + c * j * gY[0];
+            Z[1] = b2 + dPX[2] + dPY[3] + c * i * gX[1] + c * j * gY[1];
+            Z[2] = gX[0] + c * i * gX[2] + c * j * gY[2];
+            Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
+            Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
+            Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
+            /* Eqs. (19)-(20): delta P^q = C : Z_F */
+            for (m = 0; m < 4; ++m) {
+                dP[m] = 0.0;
+                for (mm = 0; mm < 4; ++mm) dP[m] += Ct[m * 4 + mm] * Z[2 + mm];
+            }
+            /* Eq. (21) */
+            D[0] = 0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1]));
+            D[1] = 0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3]));
+            D[2] = 0.25 * (Z[2] - (2.0 * i / c) * Z[0]);
+            D[3] = 0.25 * (Z[3] - (2.0 * j / c) * Z[0]);
+            D[4] = 0.25 * (Z[4] - (2.0 * i / c) * Z[1]);
+            D[5] = 0.25 * (Z[5] - (2.0 * j / c) * Z[1]);
+            for (k = 0; k < 6; ++k) f[q * 6 + k] -= 0.5 * dt * D[k];
+        }
+    }
+    return st;
+}
+
 int orc_init(orc *o, const double *U0, const double *u0, int order, const double *dUdX,
              const double *dUdY)
 {
     const long N = o->N;
-    const double c = o->c, dt = o->dt;
-    int ix, iy, q, k, m, mm;
+    const double dt = o->dt;
+    int ix, iy, q, k;
     int rc = check_edges(o);
     if (rc) return rc;
     if (o->law < 0) return -4;
@@ -502,58 +560,12 @@ int orc_init(orc *o, const double *U0, const double *u0, int order, const double
     for (iy = 0; iy < o->ny; ++iy)
         for (ix = 0; ix < o->nx; ++ix) {
             const long n = nid(o, ix, iy);
-            double U[6], F[4], P[4], feq[24], pb[8];
-            const double *prm = node_prm(o, n, pb);
-            for (k = 0; k < 6; ++k) U[k] = U0[k * N + n];
-            for (m = 0; m < 4; ++m) F[m] = U[2 + m];
-            if (orc_piola(o->law, prm, F, P) != 0) o->status |= ORC_BAD_J;
-            orc_feq(U, P, c, feq);
+            double f[24];
+            o->status |= init_at(o, U0, order, dUdX, dUdY, ix, iy, f);
             for (q = 0; q < 4; ++q)
-                for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = feq[q * 6 + k];
-            if (order == 2) {
-                double gX[6], gY[6], Ct[16], dPX[4], dPY[4];
-                const double b1 = bforce(o, 0, n), b2 = bforce(o, 1, n);
-                for (k = 0; k < 6; ++k) {
-                    gX[k] = dUdX ? dUdX[k * N + n] : fd(o, U0 + k * N, ix, iy, 0);
-                    gY[k] = dUdY ? dUdY[k * N + n] : fd(o, U0 + k * N, ix, iy, 1);
-                }
-                orc_tangent(o->law, prm, F, Ct);
-                /* d_alpha P_iA = C_iAkB d_alpha F_kB (text after Eq. 18) */
-                for (m = 0; m < 4; ++m) {
-                    dPX[m] = 0.0;
-                    dPY[m] = 0.0;
-                    for (mm = 0; mm < 4; ++mm) {
-                        dPX[m] += Ct[m * 4 + mm] * gX[2 + mm];
-                        dPY[m] += Ct[m * 4 + mm] * gY[2 + mm];
-                    }
-                }
-                for (q = 0; q < 4; ++q) {
-                    const double i = CI[q], j = CJ[q];
-                    double Z[6], dP[4], D[6];
-                    /* Eq. (18) */
-                    Z[0] = b1 + dPX[0] + dPY[1] + c * i * gX[0] + c * j * gY[0];
-                    Z[1] = b2 + dPX[2] + dPY[3] + c * i * gX[1] + c * j * gY[1];
-                    Z[2] = gX[0] + c * i * gX[2] + c * j * gY[2];
-                    Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
-                    Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
-                    Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
-                    /* Eqs. (19)-(20): delta P^q = C : Z_F */
-                    for (m = 0; m < 4; ++m) {
-                        dP[m] = 0.0;
-                        for (mm = 0; mm < 4; ++mm) dP[m] += Ct[m * 4 + mm] * Z[2 + mm];
-                    }
-                    /* Eq. (21) */
-                    D[0] = 0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1]));
-                    D[1] = 0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3]));
-                    D[2] = 0.25 * (Z[2] - (2.0 * i / c) * Z[0]);
-                    D[3] = 0.25 * (Z[3] - (2.0 * j / c) * Z[0]);
-                    D[4] = 0.25 * (Z[4] - (2.0 * i / c) * Z[1]);
-                    D[5] = 0.25 * (Z[5] - (2.0 * j / c) * Z[1]);
-                    for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] -= 0.5 * dt * D[k];
-                }
-            }
+                for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = f[q * 6 + k];
             /* Sec. 3.5: u*^0 = u0 - (dt/2) v0 */
-            for (k = 0; k < 2; ++k) o->ustar[k * N + n] = (u0 ? u0[k * N + n] : 0.0) - 0.5 * dt * U[k];
+            for (k = 0; k < 2; ++k) o->ustar[k * N + n] = (u0 ? u0[k * N + n] : 0.0) - 0.5 * dt * U0[k * N + n];
         }
     o->step = 0;
     o->ready = 1;
@@ -904,7 +916,7 @@ int orc_adjoint(orc *o, const double *U0, int order, int nsteps, int nsens, cons
     const double dt = o->dt;
     static const int dmiss[4] = {0, 2, 1, 3}, dout[4] = {2, 0, 3, 1};
     double *fh = NULL, *uh = NULL, *fb = NULL, *fbn = NULL, *fsb = NULL, *Ub = NULL, *ub = NULL, *U0p = NULL,
-           *f0p = NULL, *f0m = NULL, *mu_save = NULL;
+           *mu_save = NULL;
     long m;
     int step, k, q, e, rc = 0;
     if (!o->mufield || o->fb_mode != ORC_FB_NODE || nsteps < 0) return -1;
@@ -920,10 +932,8 @@ int orc_adjoint(orc *o, const double *U0, int order, int nsteps, int nsens, cons
     Ub = (double *)calloc((size_t)6 * N, sizeof(double));
     ub = (double *)calloc((size_t)2 * N, sizeof(double));
     U0p = (double *)malloc((size_t)6 * N * sizeof(double));
-    f0p = (double *)malloc((size_t)24 * N * sizeof(double));
-    f0m = (double *)malloc((size_t)24 * N * sizeof(double));
     mu_save = (double *)malloc((size_t)N * sizeof(double));
-    if (!fh || !uh || !fb || !fbn || !fsb || !Ub || !ub || !U0p || !f0p || !f0m || !mu_save) {
+    if (!fh || !uh || !fb || !fbn || !fsb || !Ub || !ub || !U0p || !mu_save) {
         rc = -2;
         goto done;
     }
@@ -1092,34 +1102,48 @@ int orc_adjoint(orc *o, const double *U0, int order, int nsteps, int nsens, cons
             fbn = t;
         }
     }
-    /* init: f^0 = init(U0; mu), u*^0 = u0 - (dt/2) v0 */
+    /* init: f^0 = init(U0; mu), u*^0 = u0 - (dt/2) v0. f^0 at node j depends
+     * on U0 at j and at the nodes of its finite-difference stencils (same row
+     * or column, at most two away) and on mu at j only */
     memcpy(mu_save, o->mufield, (size_t)N * sizeof(double));
+    memcpy(U0p, U0, (size_t)6 * N * sizeof(double));
     for (m = 0; m < N; ++m) {
-        int cc;
+        const int mx = (int)(m % o->nx), my = (int)(m / o->nx);
+        long nb[10];
+        int nn = 0, d, t, cc;
+        for (d = -2; d <= 2; ++d) {
+            int jx = mx + d, jy = my + d;
+            if (xper(o)) jx = ((jx % o->nx) + o->nx) % o->nx;
+            if (yper(o)) jy = ((jy % o->ny) + o->ny) % o->ny;
+            if (jx >= 0 && jx < o->nx) nb[nn++] = nid(o, jx, my);
+            if (d != 0 && jy >= 0 && jy < o->ny) nb[nn++] = nid(o, mx, jy);
+        }
         for (cc = 0; cc < 2; ++cc) {
             double acc = 0.0;
-            long j;
-            memcpy(U0p, U0, (size_t)6 * N * sizeof(double));
-            U0p[cc * N + m] = U0[cc * N + m] + 1.0;
-            orc_init(o, U0p, NULL, order, NULL, NULL);
-            memcpy(f0p, o->f, (size_t)24 * N * sizeof(double));
-            U0p[cc * N + m] = U0[cc * N + m] - 1.0;
-            orc_init(o, U0p, NULL, order, NULL, NULL);
-            memcpy(f0m, o->f, (size_t)24 * N * sizeof(double));
-            for (j = 0; j < 24 * N; ++j) acc += 0.5 * (f0p[j] - f0m[j]) * fb[j];
+            for (t = 0; t < nn; ++t) {
+                const long j = nb[t];
+                int dup = 0, u;
+                double fp[24], fm[24];
+                for (u = 0; u < t; ++u) dup |= (nb[u] == j);
+                if (dup) continue;
+                U0p[cc * N + m] = U0[cc * N + m] + 1.0;
+                init_at(o, U0p, order, NULL, NULL, (int)(j % o->nx), (int)(j / o->nx), fp);
+                U0p[cc * N + m] = U0[cc * N + m] - 1.0;
+                init_at(o, U0p, order, NULL, NULL, (int)(j % o->nx), (int)(j / o->nx), fm);
+                U0p[cc * N + m] = U0[cc * N + m];
+                for (u = 0; u < 24; ++u) acc += 0.5 * (fp[u] - fm[u]) * fb[(long)u * N + j];
+            }
             g_v0[cc * N + m] = acc - 0.5 * dt * ub[cc * N + m];
         }
         {
-            double acc = 0.0;
-            long j;
+            double fp[24], fm[24], acc = 0.0;
+            int u;
             o->mufield[m] = 1.5 * mu_save[m];
-            orc_init(o, U0, NULL, order, NULL, NULL);
-            memcpy(f0p, o->f, (size_t)24 * N * sizeof(double));
+            init_at(o, U0, order, NULL, NULL, mx, my, fp);
             o->mufield[m] = 0.5 * mu_save[m];
-            orc_init(o, U0, NULL, order, NULL, NULL);
-            memcpy(f0m, o->f, (size_t)24 * N * sizeof(double));
+            init_at(o, U0, order, NULL, NULL, mx, my, fm);
             o->mufield[m] = mu_save[m];
-            for (j = 0; j < 24 * N; ++j) acc += (f0p[j] - f0m[j]) / mu_save[m] * fb[j];
+            for (u = 0; u < 24; ++u) acc += (fp[u] - fm[u]) / mu_save[m] * fb[(long)u * N + m];
             g_mu[m] += acc;
         }
     }
@@ -1136,8 +1160,6 @@ done:
     free(Ub);
     free(ub);
     free(U0p);
-    free(f0p);
-    free(f0m);
     free(mu_save);
     return rc;
 }
