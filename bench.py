@@ -18,8 +18,10 @@ Reported (one JSON line on rank 0):
             over its mean event-timed launch duration, against the measured
             HBM copy bandwidth;
   forms     the same step with FP64, BF16 and FP16 population storage, the
-            8192^2 periodic workload in FP32 and BF16, and 256 specimens of
-            uneven size and material in batched launches (FP32);
+            8192^2 periodic workload in FP32 and BF16, 256 specimens of
+            uneven size and material in batched launches (FP32), and the
+            adjoint's cost relative to the forward on the 1024^2
+            differentiation workload (FP32, 2000 steps);
   cpu_baseline  the FP64 CPU oracle on a bounded sample (512 x 256 scaled
             specimen) on one host core.
 --impl reference times the oracle alone as the reference arm.
@@ -289,6 +291,7 @@ def run_ours(args, rank, ws, dist):
         del Up, up
 
         forms["batch_256_specimens_fp32"] = batch_form(lbm, torch, peak, k)
+        forms["adjoint_1024x1024_fp32"] = adjoint_form(lbm, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -369,6 +372,48 @@ def batch_form(lbm, torch, peak, steps, graph_steps=20):
             "value_default_tiles": nodes * steps / (ms_default * 1e-3) / 1e6,
             "note": "seed-2 specimens, N log-uniform 64^2..1024^2, aspect 1..4, NH mu U(0.2,2), lambda/mu "
                     "U(1,4), clamped left, other edges clamped or traction-free; GB/s over the whole step"}
+
+
+def adjoint_form(lbm, torch, steps=2000):
+    """Gradient of the right-edge sensor misfit with respect to mu(X) and v0
+    on the 1024^2 differentiation workload (FP32, 2000 steps, sqrt(N)
+    checkpoints): device time of the forward (with checkpoints and sensor
+    reads) and of the backward (segment recomputation included), per step,
+    and their ratio; also the ratio with every state kept (no recomputation)."""
+    from synth.generators import adjoint_specimen
+
+    w = adjoint_specimen(steps=steps)
+    p = w.params
+    U0, _ = w.fields()
+    U0d = torch.from_numpy(U0).cuda()
+    out = {}
+    for name, K in (("sqrtN", 0), ("all_states", 1)):
+        L = lbm.Lattice(w.nx, w.ny, dx=w.dx, c=w.c, omega=w.omega, storage=lbm.LBM_STORE_F32)
+        lbm.lbm_set_material_field(L.ctx, lbm.LBM_LAW_NH, p["mu"], p["lam_ratio"])
+        kinds = {"velocity": lbm.LBM_BC_VELOCITY, "traction": lbm.LBM_BC_TRACTION}
+        for e, E in enumerate(w.edges):
+            lbm.lbm_set_boundary(L.ctx, e, kinds[E.kind], E.value)
+        A = lbm.lbm_adjoint_create(L.ctx, steps, K)
+        lbm.lbm_adjoint_set_loss(A, p["sensors"], p["records"], p["target"])
+        gmu = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
+        gv0 = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device="cuda")
+        for _ in range(2):  # the first pass warms up
+            loss = lbm.lbm_adjoint_forward(A, U0d)
+            lbm.lbm_adjoint_backward(A, gmu, gv0)
+        info = lbm.lbm_adjoint_info(A)
+        lbm.lbm_adjoint_destroy(A)
+        L.close()
+        out[name] = {"checkpoint_every": info["checkpoint_every"], "stored_states": info["stored_states"],
+                     "forward_ms_per_step": info["forward_ms"] / steps,
+                     "backward_ms_per_step": info["backward_ms"] / steps,
+                     "adjoint_over_forward": info["backward_ms"] / info["forward_ms"], "loss": loss}
+    N = w.nx * w.ny
+    r = out["sqrtN"]
+    return {"value": r["adjoint_over_forward"], "unit": "backward time / forward time", "steps": steps,
+            "forward_MLUPS": N / (r["forward_ms_per_step"] * 1e-3) / 1e6,
+            "backward_MLUPS": N / (r["backward_ms_per_step"] * 1e-3) / 1e6, "checkpointing": out,
+            "note": "1024^2 clamped-left specimen, mu = exp(0.3 GRF, corr 64), lambda = 2 mu, velocity pulse, "
+                    "64 right-edge sensors recorded every 20 steps; backward includes segment recomputation"}
 
 
 def oracle_sample(nx=512, ny=256):

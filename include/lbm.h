@@ -126,9 +126,21 @@ void lbm_destroy(lbm_ctx *ctx);
  * lbm_diagnostics_state_noalloc). Valid until the next call on ctx. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A). Must be
- * called before lbm_init. LBM_ERR_UNSUPPORTED for MR, YEOH, GENT. */
+/* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A). Needed
+ * before lbm_init; set later, it applies from the next step on (the lattice
+ * speed is not checked again). Waits for the context's queued work. Replaces
+ * a material field. LBM_ERR_UNSUPPORTED for MR, YEOH, GENT. */
 lbm_status lbm_set_material(lbm_ctx *ctx, int32_t law, const double *params, int32_t nparams);
+
+/* Per-node material (the paper's closures are pointwise, so Eq. (14) takes
+ * them node by node): shear modulus mu (host, N values, finite and > 0) and
+ * lambda = lam_ratio * mu, for the SVK, NH or LOGNH closure. Replaces any
+ * uniform material (lbm_set_material replaces the field). FP64 and FP32
+ * storage only (LBM_ERR_UNSUPPORTED otherwise). Set before lbm_init (the
+ * lattice-speed check of lbm_init uses the stiffest node); set later, it
+ * applies from the next step on. Copied; waits for the upload. Contexts with
+ * a field cannot join a batch. */
+lbm_status lbm_set_material_field(lbm_ctx *ctx, int32_t law, const double *mu, double lam_ratio);
 
 /* Uniform body acceleration b = (b1, b2) of Eq. (1); B = (b1, b2, 0, 0, 0, 0)
  * enters the state recovery (Eq. 10) and the collision source (Eq. 14).
@@ -294,6 +306,56 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps, int32_t graph_steps, int
 /* Total nodes of the members, kernel launches per step and graphs captured
  * so far (any may be NULL). No device work. */
 lbm_status lbm_batch_info(const lbm_batch *b, int64_t *nodes, int32_t *launches_per_step, int32_t *graphs);
+
+/* ------------------------------------------------------------ adjoint
+ * Gradients of the sensor-displacement misfit
+ *     L = 1/2 sum_k sum_s | u(X_s, t^{n_k}) - d_{k,s} |^2
+ * (u from Eq. (22), sensors X_s at nodes, recorded steps n_k) with respect to
+ * the shear-modulus field mu(X) of lbm_set_material_field (lambda = lam_ratio
+ * mu throughout) and the initial velocity v0, by the discrete adjoint of the
+ * whole run: init (Eqs. 16-21), nsteps steps (collision, streaming, the
+ * half-way edges of Eqs. 23-25 with the traction Newton solve differentiated
+ * by the implicit function theorem, the quadrature of Eq. 22). The paper has
+ * no adjoint; the gradient is that of the discrete scheme as implemented.
+ * F0 is held fixed (only v0 of the initial state is differentiated).
+ *
+ * The forward pass stores the state every checkpoint_every steps (0 = the
+ * ceiling of sqrt(nsteps)); the backward pass recomputes each segment from
+ * its checkpoint. Device memory: (number of checkpoints + checkpoint_every
+ * - 1 + 2) population buffers. Needs FP64 or FP32 storage and the node form
+ * of F^b (LBM_ERR_UNSUPPORTED otherwise) and a material field
+ * (LBM_ERR_STATE). The object drives the context it was created on; the
+ * context must outlive it. */
+typedef struct lbm_adjoint lbm_adjoint; /* opaque, owned by the library */
+
+/* Errors of create are reported by lbm_adjoint_last_error(NULL). Allocates
+ * the checkpoint storage. */
+lbm_status lbm_adjoint_create(lbm_ctx *ctx, int64_t nsteps, int32_t checkpoint_every, lbm_adjoint **out);
+void lbm_adjoint_destroy(lbm_adjoint *adj);
+const char *lbm_adjoint_last_error(const lbm_adjoint *adj);
+
+/* sens_xy: host, nsens (x, y) node pairs, distinct; rec_steps: host, nrec
+ * distinct steps in [0, nsteps]; target: host, nrec * nsens * 2 values d,
+ * index (k * nsens + s) * 2 + component. Copied. */
+lbm_status lbm_adjoint_set_loss(lbm_adjoint *adj, int32_t nsens, const int32_t *sens_xy, int32_t nrec,
+                                const int32_t *rec_steps, const double *target);
+
+/* Initialises the context from U0_dev (device, 6N, as lbm_init_device, u0 =
+ * 0) with the given init order, runs nsteps steps storing checkpoints and
+ * sensor readings, and returns L in *loss (host). Synchronises. The context
+ * then holds the state after nsteps steps. */
+lbm_status lbm_adjoint_forward(lbm_adjoint *adj, const double *U0_dev, int32_t order, double *loss);
+
+/* dL/dmu into g_mu_dev (device, N) and dL/dv0 into g_v0_dev (device, 2N,
+ * component-major v1 then v2), for the last lbm_adjoint_forward; the context
+ * must not have been stepped since (LBM_ERR_STATE). Synchronises. */
+lbm_status lbm_adjoint_backward(lbm_adjoint *adj, double *g_mu_dev, double *g_v0_dev);
+
+/* Checkpoint interval, number of stored population buffers, and the device
+ * time of the last forward and backward passes in milliseconds (CUDA events
+ * on the context's stream; 0 if not run). Any pointer may be NULL. */
+lbm_status lbm_adjoint_info(const lbm_adjoint *adj, int32_t *checkpoint_every, int64_t *stored_states,
+                            double *forward_ms, double *backward_ms);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,493 @@
+// lbm_adjoint.cu -- the adjoint entry points of include/lbm.h: gradients of a
+// sensor-displacement misfit with respect to the per-node shear modulus and
+// the initial velocity, by the discrete adjoint of the step with checkpoints.
+//
+// Forward: init and nsteps steps on the context's own buffers; the state
+// f*^n (with its ghost cells) is copied to checkpoint n / K whenever n is a
+// multiple of K, and the sensors are read at the recorded steps.
+// Backward, segment by segment from the last: the states of the segment are
+// recomputed from its checkpoint into K - 1 slots (the step kernel, writing
+// u* and status into scratch), then for n = s1 - 1 .. s0 the adjoint kernel
+// maps a^{n+1} to a^n, the edge kernel completes a^n at the boundary and, at
+// a recorded step, the loss terms are added. Finally the init is transposed.
+// K = ceil(sqrt(nsteps)) by default: about 2 sqrt(nsteps) stored states and
+// one recomputed forward step per backward step.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace tlv;
+
+struct lbm_adjoint {
+    lbm_ctx *c = nullptr;
+    long long nsteps = 0;
+    int K = 1;
+    size_t fbytes = 0;
+    std::vector<void *> ck;    // checkpoints f*^{kK}
+    std::vector<void *> slot;  // recomputed states of one segment
+    void *A[2] = {nullptr, nullptr};
+    void *ubar = nullptr;      // compute type, 2 planes (u* layout)
+    double *gmu = nullptr;     // plane (u* layout)
+    double *ustar_scr = nullptr;
+    int *status_scr = nullptr;
+    double *U0 = nullptr;      // copy of the initial state (6N)
+    double *ghat = nullptr;    // 4N
+    int order = 2;
+    // loss
+    int nsens = 0;
+    int *d_sens = nullptr;     // (x, y) pairs
+    std::vector<int> rec_steps;
+    std::vector<int> rec_at;   // record index of step n, or -1 (nsteps + 1)
+    double *d_tgt = nullptr;   // [nrec][nsens][2]
+    double *d_rec = nullptr;
+    std::vector<double> h_tgt;
+    bool forward_done = false;
+    long long fwd_step = -1;   // the context's step count after the forward
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::string err;
+};
+
+static thread_local std::string g_adj_err;
+
+namespace {
+
+lbm_status afail(lbm_adjoint *a, lbm_status s, const std::string &msg)
+{
+    if (a)
+        a->err = msg;
+    else
+        g_adj_err = msg;
+    return s;
+}
+
+lbm_status acuda(lbm_adjoint *a, cudaError_t e, const char *what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return afail(a, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, msg);
+}
+
+#define AK(a, call)                                                         \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return acuda((a), e_, #call);                \
+    } while (0)
+
+bool fp64(const lbm_adjoint *a) { return a->c->cfg.storage == LBM_STORE_F64; }
+
+template <typename T>
+AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, const void *ain, void *aout)
+{
+    const lbm_ctx *c = a->c;
+    const double w = c->cfg.omega;
+    AdjArgs<T> r;
+    r.fin = fin;
+    r.ain = ain;
+    r.aout = aout;
+    r.mufield = static_cast<const T *>(c->d_muplane);
+    r.ubar = static_cast<const T *>(a->ubar);
+    r.gmu = a->gmu;
+    r.L = c->L;
+    r.one_m_omega = (T)(1.0 - w);
+    r.wq = (T)(0.25 * w);
+    r.wi2c = (T)(0.5 * w / c->cfg.c);
+    r.wi2c_d = 0.5 * w / c->cfg.c;
+    r.dtT = (T)c->dt;
+    r.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
+    r.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
+    r.lam_ratio = (T)c->m.lam_ratio;
+    return r;
+}
+
+int ring_count(const Layout &L)
+{
+    const int rows = L.ny > 1 ? 2 : 1;
+    const int cols = L.nx > 1 ? 2 : 1;
+    return rows * L.nx + (L.ny > 2 ? (L.ny - 2) * cols : 0);
+}
+
+// the ghosts of f*^n hold edge data at t^n + dt/2
+template <typename T>
+FoldArgs<T> fold_args(const lbm_adjoint *a, const void *fin, void *aout, long long n)
+{
+    const lbm_ctx *c = a->c;
+    FoldArgs<T> r;
+    r.fin = fin;
+    r.aout = aout;
+    r.mufield = static_cast<const T *>(c->d_muplane);
+    r.gmu = a->gmu;
+    r.L = c->L;
+    for (int e = 0; e < 4; ++e) {
+        r.kind[e] = c->edge[e].kind;
+        r.value[e][0] = c->edge[e].value[0];
+        r.value[e][1] = c->edge[e].value[1];
+        r.g[e] = ctx_time_factor(c, e, n - 1);
+        r.profile[e] = c->edge[e].profile;
+    }
+    r.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
+    r.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
+    r.lam_ratio = (T)c->m.lam_ratio;
+    r.count = ring_count(c->L);
+    return r;
+}
+
+lbm_status record(lbm_adjoint *a, int k)
+{
+    lbm_ctx *c = a->c;
+    RecordArgs r;
+    r.f = c->f[c->cur];
+    r.ustar = c->ustar;
+    r.sens = a->d_sens;
+    r.out = a->d_rec + (size_t)k * a->nsens * 2;
+    r.nsens = a->nsens;
+    r.L = c->L;
+    r.dt = c->dt;
+    r.b1 = c->b[0];
+    r.b2 = c->b[1];
+    AK(a, launch_adj_record(c->cfg.storage, r, c->st));
+    return LBM_OK;
+}
+
+lbm_status inject(lbm_adjoint *a, void *aout, int k)
+{
+    lbm_ctx *c = a->c;
+    if (fp64(a)) {
+        InjectArgs<double> r{aout, static_cast<double *>(a->ubar), a->d_sens, a->d_rec + (size_t)k * a->nsens * 2,
+                             a->d_tgt + (size_t)k * a->nsens * 2, a->nsens, c->L, c->dt};
+        AK(a, launch_adj_inject(c->cfg.storage, &r, c->st));
+    } else {
+        InjectArgs<float> r{aout, static_cast<float *>(a->ubar), a->d_sens, a->d_rec + (size_t)k * a->nsens * 2,
+                            a->d_tgt + (size_t)k * a->nsens * 2, a->nsens, c->L, c->dt};
+        AK(a, launch_adj_inject(c->cfg.storage, &r, c->st));
+    }
+    return LBM_OK;
+}
+
+// one forward step from buffer fin (state n) into fout, u* and status into scratch
+lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long n)
+{
+    lbm_ctx *c = a->c;
+    if (fp64(a)) {
+        StepArgs<double> s = ctx_step_args<double>(c, c->cur);
+        s.fin = fin;
+        s.fout = fout;
+        s.ustar = a->ustar_scr;
+        s.status = a->status_scr;
+        for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
+    } else {
+        StepArgs<float> s = ctx_step_args<float>(c, c->cur);
+        s.fin = fin;
+        s.fout = fout;
+        s.ustar = a->ustar_scr;
+        s.status = a->status_scr;
+        for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
+    }
+    return LBM_OK;
+}
+
+lbm_status adjoint_step(lbm_adjoint *a, const void *fin, const void *ain, void *aout, long long n, int grid)
+{
+    lbm_ctx *c = a->c;
+    if (fp64(a)) {
+        const AdjArgs<double> r = adj_args<double>(a, fin, ain, aout);
+        AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
+        const FoldArgs<double> fr = fold_args<double>(a, fin, aout, n);
+        AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
+    } else {
+        const AdjArgs<float> r = adj_args<float>(a, fin, ain, aout);
+        AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
+        const FoldArgs<float> fr = fold_args<float>(a, fin, aout, n);
+        AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
+    }
+    return LBM_OK;
+}
+
+void free_all(lbm_adjoint *a)
+{
+    for (void *p : a->ck) cudaFree(p);
+    for (void *p : a->slot) cudaFree(p);
+    a->ck.clear();
+    a->slot.clear();
+    cudaFree(a->A[0]);
+    cudaFree(a->A[1]);
+    cudaFree(a->ubar);
+    cudaFree(a->gmu);
+    cudaFree(a->ustar_scr);
+    cudaFree(a->status_scr);
+    cudaFree(a->U0);
+    cudaFree(a->ghat);
+    cudaFree(a->d_sens);
+    cudaFree(a->d_tgt);
+    cudaFree(a->d_rec);
+    for (cudaEvent_t &e : a->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+} // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint_create(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_every, lbm_adjoint **out)
+{
+    if (!out) return afail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!c) return afail(nullptr, LBM_ERR_ARG, "null context");
+    if (nsteps < 0 || nsteps > (1LL << 30)) return afail(nullptr, LBM_ERR_ARG, "nsteps out of range");
+    if (checkpoint_every < 0) return afail(nullptr, LBM_ERR_ARG, "checkpoint_every must be >= 0");
+    if (!c->m.mufield) return afail(nullptr, LBM_ERR_STATE, "the context needs a material field (lbm_set_material_field)");
+    if (c->cfg.storage != LBM_STORE_F64 && c->cfg.storage != LBM_STORE_F32)
+        return afail(nullptr, LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 or FP32 storage");
+    if (c->cfg.fb_mode != LBM_FB_NODE) return afail(nullptr, LBM_ERR_UNSUPPORTED, "the adjoint needs the node form of F^b");
+    lbm_adjoint *a = new (std::nothrow) lbm_adjoint();
+    if (!a) return afail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    a->c = c;
+    a->nsteps = nsteps;
+    a->K = checkpoint_every > 0 ? checkpoint_every
+                                : std::max(1, (int)std::ceil(std::sqrt((double)std::max<long long>(nsteps, 1))));
+    a->fbytes = (size_t)24 * (size_t)c->L.plane * c->eb;
+    a->rec_at.assign((size_t)nsteps + 1, -1);
+    const int R = (c->cfg.storage == LBM_STORE_F64) ? 8 : 4;
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    const long long nck = nsteps > 0 ? (nsteps - 1) / a->K + 1 : 0;
+    lbm_status s = LBM_OK;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (s != LBM_OK) return;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) s = acuda(a, e, "cudaMalloc");
+    };
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e != cudaSuccess) s = acuda(a, e, "cudaSetDevice");
+    a->ck.assign((size_t)nck, nullptr);
+    for (auto &p : a->ck) alloc(&p, a->fbytes);
+    a->slot.assign((size_t)std::max(0, a->K - 1), nullptr);
+    for (auto &p : a->slot) alloc(&p, a->fbytes);
+    alloc(&a->A[0], a->fbytes);
+    alloc(&a->A[1], a->fbytes);
+    alloc(&a->ubar, (size_t)2 * c->L.uplane * R);
+    alloc((void **)&a->gmu, (size_t)c->L.uplane * sizeof(double));
+    alloc((void **)&a->ustar_scr, (size_t)2 * c->L.uplane * sizeof(double));
+    alloc((void **)&a->status_scr, sizeof(int));
+    alloc((void **)&a->U0, 6 * N * sizeof(double));
+    alloc((void **)&a->ghat, 4 * N * sizeof(double));
+    for (cudaEvent_t &ev : a->ev)
+        if (s == LBM_OK && cudaEventCreate(&ev) != cudaSuccess) s = afail(a, LBM_ERR_CUDA, "cudaEventCreate");
+    if (s == LBM_OK) {
+        e = cudaMemsetAsync(a->ustar_scr, 0, (size_t)2 * c->L.uplane * sizeof(double), c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a->status_scr, 0, sizeof(int), c->st);
+        // slots and adjoint buffers: ghosts and padding start defined
+        for (void *p : a->slot)
+            if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, a->fbytes, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) s = acuda(a, e, "cudaMemsetAsync");
+    }
+    if (s != LBM_OK) {
+        g_adj_err = a->err;
+        free_all(a);
+        delete a;
+        return s;
+    }
+    *out = a;
+    return LBM_OK;
+}
+
+void lbm_adjoint_destroy(lbm_adjoint *a)
+{
+    if (!a) return;
+    cudaSetDevice(a->c->cfg.device);
+    cudaStreamSynchronize(a->c->st);
+    free_all(a);
+    delete a;
+}
+
+const char *lbm_adjoint_last_error(const lbm_adjoint *a) { return a ? a->err.c_str() : g_adj_err.c_str(); }
+
+lbm_status lbm_adjoint_set_loss(lbm_adjoint *a, int32_t nsens, const int32_t *sens_xy, int32_t nrec,
+                                const int32_t *rec_steps, const double *target)
+{
+    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
+    lbm_ctx *c = a->c;
+    if (nsens < 1 || nrec < 1 || !sens_xy || !rec_steps || !target)
+        return afail(a, LBM_ERR_ARG, "need at least one sensor and one record, and non-NULL arrays");
+    std::vector<long long> seen;
+    for (int s = 0; s < nsens; ++s) {
+        const int x = sens_xy[2 * s], y = sens_xy[2 * s + 1];
+        if (x < 0 || x >= c->L.nx || y < 0 || y >= c->L.ny) return afail(a, LBM_ERR_ARG, "sensor outside the lattice");
+        seen.push_back((long long)y * c->L.nx + x);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return afail(a, LBM_ERR_ARG, "a sensor node appears twice");
+    std::vector<int> at((size_t)a->nsteps + 1, -1);
+    for (int k = 0; k < nrec; ++k) {
+        if (rec_steps[k] < 0 || rec_steps[k] > a->nsteps) return afail(a, LBM_ERR_ARG, "recorded step outside [0, nsteps]");
+        if (at[rec_steps[k]] >= 0) return afail(a, LBM_ERR_ARG, "a step is recorded twice");
+        at[rec_steps[k]] = k;
+    }
+    for (size_t i = 0; i < (size_t)nrec * nsens * 2; ++i)
+        if (!std::isfinite(target[i])) return afail(a, LBM_ERR_ARG, "targets must be finite");
+    AK(a, cudaSetDevice(c->cfg.device));
+    cudaFree(a->d_sens);
+    cudaFree(a->d_tgt);
+    cudaFree(a->d_rec);
+    a->d_sens = nullptr;
+    a->d_tgt = a->d_rec = nullptr;
+    AK(a, cudaMalloc((void **)&a->d_sens, (size_t)2 * nsens * sizeof(int)));
+    AK(a, cudaMalloc((void **)&a->d_tgt, (size_t)nrec * nsens * 2 * sizeof(double)));
+    AK(a, cudaMalloc((void **)&a->d_rec, (size_t)nrec * nsens * 2 * sizeof(double)));
+    AK(a, cudaMemcpy(a->d_sens, sens_xy, (size_t)2 * nsens * sizeof(int), cudaMemcpyHostToDevice));
+    AK(a, cudaMemcpy(a->d_tgt, target, (size_t)nrec * nsens * 2 * sizeof(double), cudaMemcpyHostToDevice));
+    a->nsens = nsens;
+    a->rec_steps.assign(rec_steps, rec_steps + nrec);
+    a->rec_at = at;
+    a->h_tgt.assign(target, target + (size_t)nrec * nsens * 2);
+    a->forward_done = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t order, double *loss)
+{
+    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
+    if (!loss) return afail(a, LBM_ERR_ARG, "loss is NULL");
+    if (a->nsens < 1) return afail(a, LBM_ERR_STATE, "lbm_adjoint_set_loss must come first");
+    lbm_ctx *c = a->c;
+    if (!c->m.mufield) return afail(a, LBM_ERR_STATE, "the context lost its material field");
+    AK(a, cudaSetDevice(c->cfg.device));
+    a->forward_done = false;
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    AK(a, cudaEventRecord(a->ev[0], c->st));
+    lbm_status s = lbm_init_device(c, U0_dev, nullptr, order);
+    if (s != LBM_OK) return afail(a, s, "init: " + c->err);
+    a->order = order;
+    AK(a, cudaMemcpyAsync(a->U0, U0_dev, 6 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    s = ctx_refresh_ghosts(c);
+    if (s != LBM_OK) return afail(a, s, c->err);
+    const long long n0 = c->step;  // 0 after init
+    for (long long n = 0; n <= a->nsteps; ++n) {
+        if (n > 0) {
+            s = lbm_step_async(c, 1);
+            if (s != LBM_OK) return afail(a, s, c->err);
+        }
+        if (n < a->nsteps && n % a->K == 0)
+            AK(a, cudaMemcpyAsync(a->ck[(size_t)(n / a->K)], c->f[c->cur], a->fbytes, cudaMemcpyDeviceToDevice, c->st));
+        if (a->rec_at[(size_t)n] >= 0) {
+            s = record(a, a->rec_at[(size_t)n]);
+            if (s != LBM_OK) return s;
+        }
+    }
+    AK(a, cudaEventRecord(a->ev[1], c->st));
+    s = lbm_sync(c);
+    if (s != LBM_OK) return afail(a, s, c->err);
+    const size_t nr = a->rec_steps.size() * a->nsens * 2;
+    std::vector<double> rec(nr);
+    AK(a, cudaMemcpy(rec.data(), a->d_rec, nr * sizeof(double), cudaMemcpyDeviceToHost));
+    double L = 0.0;
+    for (size_t i = 0; i < nr; ++i) {
+        const double r = rec[i] - a->h_tgt[i];
+        L += 0.5 * r * r;
+    }
+    *loss = L;
+    a->forward_done = true;
+    a->fwd_step = n0 + a->nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
+{
+    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
+    if (!g_mu_dev || !g_v0_dev) return afail(a, LBM_ERR_ARG, "output pointers must be non-NULL");
+    lbm_ctx *c = a->c;
+    if (!a->forward_done || c->step != a->fwd_step)
+        return afail(a, LBM_ERR_STATE, "lbm_adjoint_forward must precede, with no other step of the context between");
+    AK(a, cudaSetDevice(c->cfg.device));
+    const int R = fp64(a) ? 8 : 4;
+    AK(a, cudaEventRecord(a->ev[2], c->st));
+    AK(a, cudaMemsetAsync(a->A[0], 0, a->fbytes, c->st));
+    AK(a, cudaMemsetAsync(a->A[1], 0, a->fbytes, c->st));
+    AK(a, cudaMemsetAsync(a->ubar, 0, (size_t)2 * c->L.uplane * R, c->st));
+    AK(a, cudaMemsetAsync(a->gmu, 0, (size_t)c->L.uplane * sizeof(double), c->st));
+    int cur = 0;
+    lbm_status s = LBM_OK;
+    if (a->rec_at[(size_t)a->nsteps] >= 0) s = inject(a, a->A[cur], a->rec_at[(size_t)a->nsteps]);
+    if (s != LBM_OK) return s;
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    const int per_sm = std::max(1, adj_blocks_per_sm(c->cfg.storage, c->m.law));
+    const int vec = adj_vec_for(c->cfg.storage);
+    const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
+    const int grid = (int)std::max(1LL, std::min((tasks + 3) / 4, (long long)sms * per_sm));
+    const long long nck = (long long)a->ck.size();
+    for (long long k = nck - 1; k >= 0; --k) {
+        const long long s0 = k * a->K, s1 = std::min(s0 + a->K, a->nsteps);
+        auto state = [&](long long n) -> const void * { return n == s0 ? a->ck[(size_t)k] : a->slot[(size_t)(n - s0 - 1)]; };
+        for (long long n = s0 + 1; n < s1; ++n) {
+            s = recompute_step(a, state(n - 1), a->slot[(size_t)(n - s0 - 1)], n - 1);
+            if (s != LBM_OK) return s;
+        }
+        for (long long n = s1 - 1; n >= s0; --n) {
+            s = adjoint_step(a, state(n), a->A[cur], a->A[cur ^ 1], n, grid);
+            if (s != LBM_OK) return s;
+            cur ^= 1;
+            if (a->rec_at[(size_t)n] >= 0) {
+                s = inject(a, a->A[cur], a->rec_at[(size_t)n]);
+                if (s != LBM_OK) return s;
+            }
+        }
+    }
+    // the init (its u* and its collision included)
+    AdjInitArgs ai;
+    std::memset(&ai, 0, sizeof ai);
+    ai.ia.U0 = a->U0;
+    ai.ia.u0 = nullptr;
+    ai.ia.fout = nullptr;
+    ai.ia.ustar = nullptr;
+    ai.ia.status = nullptr;
+    ai.ia.L = c->L;
+    ai.ia.m = c->m;
+    ai.ia.c = c->cfg.c;
+    ai.ia.dt = c->dt;
+    ai.ia.dx = c->cfg.dx;
+    ai.ia.omega = c->cfg.omega;
+    ai.ia.b1 = c->b[0];
+    ai.ia.b2 = c->b[1];
+    ai.ia.order = a->order;
+    ai.ia.xper = c->edge[LBM_EDGE_LEFT].kind == LBM_BC_PERIODIC;
+    ai.ia.yper = c->edge[LBM_EDGE_BOTTOM].kind == LBM_BC_PERIODIC;
+    ai.a0 = a->A[cur];
+    ai.ubar = a->ubar;
+    ai.gmu = a->gmu;
+    ai.gv0 = g_v0_dev;
+    ai.ghat = a->ghat;
+    AK(a, launch_adj_init(c->cfg.storage, ai, c->st));
+    AK(a, launch_plane_to_compact(a->gmu, g_mu_dev, c->L, c->st));
+    AK(a, cudaEventRecord(a->ev[3], c->st));
+    AK(a, cudaStreamSynchronize(c->st));
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_info(const lbm_adjoint *a, int32_t *checkpoint_every, int64_t *stored_states,
+                            double *forward_ms, double *backward_ms)
+{
+    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
+    if (checkpoint_every) *checkpoint_every = a->K;
+    if (stored_states) *stored_states = (int64_t)(a->ck.size() + a->slot.size());
+    float f = 0.f, b = 0.f;
+    if (forward_ms) {
+        *forward_ms = 0.0;
+        if (a->forward_done && cudaEventElapsedTime(&f, a->ev[0], a->ev[1]) == cudaSuccess) *forward_ms = f;
+    }
+    if (backward_ms) {
+        *backward_ms = 0.0;
+        if (cudaEventQuery(a->ev[3]) == cudaSuccess && cudaEventElapsedTime(&b, a->ev[2], a->ev[3]) == cudaSuccess)
+            *backward_ms = b;
+        cudaGetLastError();
+    }
+    return LBM_OK;
+}
+
+} // extern "C"

@@ -114,6 +114,8 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.src2 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[1]);
     a.lam = (T)c->m.lam;
     a.mu = (T)c->m.mu;
+    a.mufield = static_cast<const T *>(c->d_muplane);
+    a.lam_ratio = (T)c->m.lam_ratio;
     a.c = (T)c->cfg.c;
     a.dt = c->dt;
     for (int e = 0; e < 4; ++e) {
@@ -299,6 +301,30 @@ lbm_status refresh_ghosts(lbm_ctx *c)
 
 } // namespace
 
+static void drop_material_field(lbm_ctx *c)
+{
+    cudaFree(c->d_mufield);
+    cudaFree(c->d_muplane);
+    c->d_mufield = nullptr;
+    c->d_muplane = nullptr;
+    c->m.mufield = nullptr;
+    c->m.lam_ratio = 0.0;
+}
+
+static lbm_status set_step_grid(lbm_ctx *c)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    const int per_sm = step_blocks_per_sm(c->cfg.storage, c->m.law);
+    const int vec = step_vec(c->cfg.storage);
+    const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
+    const long long needed = (tasks + 3) / 4; // 4 warps per block
+    long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (g > needed) g = needed;
+    c->grid_step = (int)(g < 1 ? 1 : g);
+    return LBM_OK;
+}
+
 namespace tlv {
 
 lbm_status ctx_fail(lbm_ctx *c, lbm_status s, const std::string &msg) { return fail(c, s, msg); }
@@ -413,6 +439,8 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_diag);
     for (int e = 0; e < 4; ++e) cudaFree(c->d_profile[e]);
+    cudaFree(c->d_mufield);
+    cudaFree(c->d_muplane);
     delete c;
 }
 
@@ -421,7 +449,6 @@ const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_cre
 lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32_t nparams)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
-    if (c->initialized) return fail(c, LBM_ERR_STATE, "the material must be set before lbm_init");
     if (law == LBM_LAW_MR || law == LBM_LAW_YEOH || law == LBM_LAW_GENT)
         return fail(c, LBM_ERR_UNSUPPORTED, "Mooney-Rivlin, Yeoh and Gent closures are not built in this version");
     if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH) return fail(c, LBM_ERR_ARG, "unknown law");
@@ -429,22 +456,53 @@ lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32
     if (!is_finite(params[0]) || !is_finite(params[1]) || !(params[1] > 0.0))
         return fail(c, LBM_ERR_ARG, "lambda must be finite and mu finite and > 0");
     if (!(params[0] + 2.0 * params[1] > 0.0)) return fail(c, LBM_ERR_ARG, "lambda + 2 mu must be > 0");
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->st));  // queued steps may still read the old field
     c->m.law = law; // LBM_LAW_* and tlv::LAW_* share values for SVK, NH, LOGNH
     c->m.lam = params[0];
     c->m.mu = params[1];
     c->have_material = true;
-    CK(c, cudaSetDevice(c->cfg.device));
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
-    const int per_sm = step_blocks_per_sm(c->cfg.storage, c->m.law);
-    const int vec = step_vec(c->cfg.storage);
-    const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
-    const long long needed = (tasks + 3) / 4; // 4 warps per block
-    long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    if (g > needed) g = needed;
-    c->grid_step = (int)(g < 1 ? 1 : g);
-    return LBM_OK;
+    c->ghosts_dirty = true;  // traction ghosts depend on the material
+    drop_material_field(c);
+    return set_step_grid(c);
 }
+
+lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, double lam_ratio)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH)
+        return fail(c, LBM_ERR_ARG, "material fields take the SVK, NH or LOGNH closure");
+    if (c->cfg.storage != LBM_STORE_F64 && c->cfg.storage != LBM_STORE_F32)
+        return fail(c, LBM_ERR_UNSUPPORTED, "material fields need FP64 or FP32 storage");
+    if (!mu) return fail(c, LBM_ERR_ARG, "mu is NULL");
+    if (!is_finite(lam_ratio) || !(lam_ratio + 2.0 > 0.0)) return fail(c, LBM_ERR_ARG, "lam_ratio must be finite and > -2");
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    double mumax = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        if (!is_finite(mu[n]) || !(mu[n] > 0.0)) return fail(c, LBM_ERR_ARG, "mu must be finite and > 0 at every node");
+        mumax = std::max(mumax, mu[n]);
+    }
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->st));  // queued steps may still read the old field
+    drop_material_field(c);
+    const size_t pbytes = (size_t)c->L.uplane * (c->cfg.storage == LBM_STORE_F64 ? 8 : 4);
+    CK(c, cudaMalloc((void **)&c->d_mufield, N * sizeof(double)));
+    CK(c, cudaMalloc(&c->d_muplane, pbytes));
+    CK(c, cudaMemsetAsync(c->d_muplane, 0, pbytes, c->st));
+    CK(c, cudaMemcpyAsync(c->d_mufield, mu, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(c, launch_mu_plane(c->cfg.storage, c->d_mufield, c->d_muplane, c->L, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    c->m.law = law;
+    c->m.mufield = c->d_mufield;
+    c->m.lam_ratio = lam_ratio;
+    // the uniform pair holds the stiffest node, for the lattice-speed check
+    c->m.mu = mumax;
+    c->m.lam = lam_ratio * mumax;
+    c->have_material = true;
+    c->ghosts_dirty = true;
+    return set_step_grid(c);
+}
+
 
 lbm_status lbm_set_body_force(lbm_ctx *c, double b1, double b2)
 {

@@ -2,49 +2,9 @@
 // vectorial D2Q4x6 LBM. All of them compute in FP64 whatever the storage.
 #include <cfloat>
 
-#include "lbm_device.cuh"
-#include "lbm_internal.h"
+#include "lbm_init_core.cuh"
 
 namespace tlv {
-
-static __device__ __forceinline__ long long pidx(const Layout &L, int q, int k, int x, int y)
-{
-    return (long long)(q * 6 + k) * L.plane + (long long)(y + 1) * L.pitch + L.xoff + x;
-}
-
-static __device__ void piola_any(int law, const double G[4], double lam, double mu, double P[4], double &dJ)
-{
-    if (law == LAW_SVK)
-        piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else if (law == LAW_NH)
-        piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else
-        piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-}
-
-// Second-order difference of a compact field along x (dir 0) or y (dir 1):
-// central inside, wrap-around when periodic, one-sided three-point stencil at
-// a non-periodic end (Sec. 3.4).
-static __device__ double fd(const double *a, int nx, int ny, int x, int y, int dir, int per, double dx)
-{
-    const int n = dir == 0 ? nx : ny;
-    const int i = dir == 0 ? x : y;
-    auto at = [&](int j) { return dir == 0 ? a[(long long)y * nx + j] : a[(long long)j * nx + x]; };
-    if (per) return (at((i + 1) % n) - at((i - 1 + n) % n)) / (2.0 * dx);
-    if (i == 0) return (-3.0 * at(0) + 4.0 * at(1) - at(2)) / (2.0 * dx);
-    if (i == n - 1) return (3.0 * at(n - 1) - 4.0 * at(n - 2) + at(n - 3)) / (2.0 * dx);
-    return (at(i + 1) - at(i - 1)) / (2.0 * dx);
-}
-
-// f^eq_q(U) of Eq. (12) in full (not offset) form
-static __device__ __forceinline__ void feq_full(const double U[6], const double P[4], double c, double feq[4][6])
-{
-    const double PhiX[6] = {-P[0], -P[2], -U[0], 0.0, -U[1], 0.0};
-    const double PhiY[6] = {-P[1], -P[3], 0.0, -U[0], 0.0, -U[1]};
-    const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
-    for (int q = 0; q < 4; ++q)
-        for (int k = 0; k < 6; ++k) feq[q][k] = 0.25 * (U[k] + (2.0 / c) * (ci[q] * PhiX[k] + cj[q] * PhiY[k]));
-}
 
 // Initial populations (Sec. 3.4) followed by the collision of step 0, so the
 // stored state is f*^0; u* receives u0 - (dt/2) v0 + dt v^0 (Eq. 22).
@@ -54,57 +14,21 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
     const int nx = a.L.nx, ny = a.L.ny;
     const long long N = (long long)nx * ny;
     T *fout = static_cast<T *>(a.fout);
-    const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
     const double c = a.c, dt = a.dt;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
-        double U[6];
-        for (int k = 0; k < 6; ++k) U[k] = a.U0[k * N + n];
-        const double F[4] = {U[2], U[3], U[4], U[5]};
-        const double G[4] = {U[2] - 1.0, U[3], U[4], U[5] - 1.0};
-        double P[4], dJ, f[4][6];
-        piola_any(a.m.law, G, a.m.lam, a.m.mu, P, dJ);
-        if (!(dJ > -1.0)) atomicOr(a.status, ST_BAD_J);
-        feq_full(U, P, c, f);
-        if (a.order == 2) {
-            double gX[6], gY[6], dPX[4], dPY[4];
-            for (int k = 0; k < 6; ++k) {
-                gX[k] = fd(a.U0 + k * N, nx, ny, x, y, 0, a.xper, a.dx);
-                gY[k] = fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, a.dx);
-            }
-            // d_alpha P = C : d_alpha F (text after Eq. 18), as Jacobian actions (Eq. 8)
-            tangent_jvp(a.m.law, F, gX + 2, a.m.lam, a.m.mu, dPX);
-            tangent_jvp(a.m.law, F, gY + 2, a.m.lam, a.m.mu, dPY);
-            for (int q = 0; q < 4; ++q) {
-                const double i = ci[q], j = cj[q];
-                double Z[6], dP[4];
-                // Eq. (18): Z_q = D_q U0 with d_t U0 taken from the continuum system
-                Z[0] = a.b1 + dPX[0] + dPY[1] + c * i * gX[0] + c * j * gY[0];
-                Z[1] = a.b2 + dPX[2] + dPY[3] + c * i * gX[1] + c * j * gY[1];
-                Z[2] = gX[0] + c * i * gX[2] + c * j * gY[2];
-                Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
-                Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
-                Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
-                tangent_jvp(a.m.law, F, Z + 2, a.m.lam, a.m.mu, dP); // Eq. (20)
-                // Eq. (21): D_q f^eq = (f^eq)'(U0) Z_q, then Eq. (16)
-                const double Dq[6] = {0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1])),
-                                      0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3])),
-                                      0.25 * (Z[2] - (2.0 * i / c) * Z[0]),
-                                      0.25 * (Z[3] - (2.0 * j / c) * Z[0]),
-                                      0.25 * (Z[4] - (2.0 * i / c) * Z[1]),
-                                      0.25 * (Z[5] - (2.0 * j / c) * Z[1])};
-                for (int k = 0; k < 6; ++k) f[q][k] -= 0.5 * dt * Dq[k];
-            }
-        }
+        double lam, mu, f[4][6];
+        mat_at(a.m, n, lam, mu);
+        if (!init_node(a, x, y, lam, mu, f)) atomicOr(a.status, ST_BAD_J);
         // step-0 collision (Eqs. 10, 12, 14)
-        double Un[6];
+        double Un[6], dJ;
         for (int k = 0; k < 6; ++k) Un[k] = f[0][k] + f[1][k] + f[2][k] + f[3][k];
         Un[0] += 0.5 * dt * a.b1;
         Un[1] += 0.5 * dt * a.b2;
         const double Gn[4] = {Un[2] - 1.0, Un[3], Un[4], Un[5] - 1.0};
         double Pn[4], feq[4][6];
-        piola_any(a.m.law, Gn, a.m.lam, a.m.mu, Pn, dJ);
+        piola_any(a.m.law, Gn, lam, mu, Pn, dJ);
         feq_full(Un, Pn, c, feq);
         const double src[2] = {dt * (2.0 - a.omega) * 0.125 * a.b1, dt * (2.0 - a.omega) * 0.125 * a.b2};
         for (int q = 0; q < 4; ++q)
@@ -115,8 +39,19 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
             }
         for (int k = 0; k < 2; ++k) {
             const double u0 = a.u0 ? a.u0[k * N + n] : 0.0;
-            a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] = (u0 - 0.5 * dt * U[k]) + dt * Un[k];
+            a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] = (u0 - 0.5 * dt * a.U0[k * N + n]) + dt * Un[k];
         }
+    }
+}
+
+template <typename R>
+__global__ void k_mu_plane(const double *mu, R *plane, Layout L)
+{
+    const long long N = (long long)L.nx * L.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.nx), y = (int)(n / L.nx);
+        plane[(long long)y * L.upitch + x] = (R)mu[n];
     }
 }
 
@@ -148,8 +83,9 @@ __global__ void __launch_bounds__(128) k_read(const ReadArgs a)
             a.U[5 * N + n] = 1.0 + G[3];
         }
         if (a.P || a.sigma) {
-            double P[4], dJ;
-            piola_any(a.m.law, G, a.m.lam, a.m.mu, P, dJ);
+            double P[4], dJ, lam, mu;
+            mat_at(a.m, n, lam, mu);
+            piola_any(a.m.law, G, lam, mu, P, dJ);
             if (a.P)
                 for (int m = 0; m < 4; ++m) a.P[m * N + n] = P[m];
             if (a.sigma) {
@@ -246,7 +182,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const DiagArgs a)
         r.s[0] += v1;
         r.s[1] += v2;
         for (int m = 0; m < 4; ++m) r.s[2 + m] += S[2 + m];
-        r.s[6] += 0.5 * (v1 * v1 + v2 * v2) + energy_ofs(a.m.law, S[2], S[3], S[4], S[5], a.m.lam, a.m.mu);
+        double lam, mu;
+        mat_at(a.m, n, lam, mu);
+        r.s[6] += 0.5 * (v1 * v1 + v2 * v2) + energy_ofs(a.m.law, S[2], S[3], S[4], S[5], lam, mu);
         r.jmin = fmin(r.jmin, 1.0 + dJ);
         r.jmax = fmax(r.jmax, 1.0 + dJ);
         r.gmax = fmax(r.gmax, sqrt(S[2] * S[2] + S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
@@ -335,6 +273,17 @@ cudaError_t launch_diag(int storage, const DiagArgs &a, cudaStream_t st)
         return 0;
     });
     k_diag_final<<<1, DIAG_THREADS, 0, st>>>(a, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_plane(int storage, const double *mu, void *plane, const Layout &L, cudaStream_t st)
+{
+    const long long N = (long long)L.nx * L.ny;
+    const int grid = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
+    if (storage == STORE_F64)
+        k_mu_plane<double><<<grid, 256, 0, st>>>(mu, static_cast<double *>(plane), L);
+    else
+        k_mu_plane<float><<<grid, 256, 0, st>>>(mu, static_cast<float *>(plane), L);
     return cudaGetLastError();
 }
 

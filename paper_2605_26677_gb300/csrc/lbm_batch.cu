@@ -355,6 +355,7 @@ lbm_status members_ready(lbm_batch *b)
     for (lbm_ctx *c : b->m) {
         lbm_status s = ctx_ready(c);
         if (s != LBM_OK) return bfail(b, s, "member not ready: " + c->err);
+        if (c->m.mufield) return bfail(b, LBM_ERR_ARG, "batches take members with uniform material");
         if (c->ghosts_dirty) {
             s = ctx_refresh_ghosts(c);
             if (s != LBM_OK) return bfail(b, s, "member ghost refresh: " + c->err);
@@ -494,6 +495,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *members, int32_t n, lbm_batch **out)
         if (c->cfg.storage != members[0]->cfg.storage)
             return bfail(nullptr, LBM_ERR_ARG, "members with different storage types");
         if (c->cfg.fb_mode != LBM_FB_NODE) return bfail(nullptr, LBM_ERR_ARG, "batches take members in the node form of F^b");
+        if (c->m.mufield) return bfail(nullptr, LBM_ERR_ARG, "batches take members with uniform material");
     }
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return bfail(nullptr, LBM_ERR_OOM, "host allocation failed");

@@ -94,7 +94,21 @@ struct Layout {
 struct Material {
     int law;
     double lam, mu;
+    const double *mufield;  // per-node mu (compact, node y * nx + x) or nullptr
+    double lam_ratio;       // lambda = lam_ratio * mu where mufield is set
 };
+
+// (lambda, mu) of node n (compact index)
+__device__ __forceinline__ void mat_at(const Material &m, long long n, double &lam, double &mu)
+{
+    if (m.mufield) {
+        mu = m.mufield[n];
+        lam = m.lam_ratio * mu;
+    } else {
+        lam = m.lam;
+        mu = m.mu;
+    }
+}
 
 struct EdgeDesc {
     int kind, timefn;
@@ -115,6 +129,8 @@ struct StepArgs {
     T hdtb1, hdtb2;              // (dt/2) b
     T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
     T lam, mu, c;
+    const T *mufield;            // per-node mu in the u* plane layout, read by the MATF kernels
+    T lam_ratio;                 // lambda = lam_ratio * mu there
     double dt;
     // edge rules, used when the kernel also writes the ghost cells of fout:
     // value * g * profile[s], g = g(t^n + dt/2) evaluated once on the host

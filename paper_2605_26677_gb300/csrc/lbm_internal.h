@@ -34,6 +34,8 @@ struct lbm_ctx {
     std::string err;
     bool prof = false;
     std::vector<cudaEvent_t> ev_step, ev_edge; // start/stop pairs
+    double *d_mufield = nullptr;  // per-node mu, compact FP64 (N), or nullptr
+    void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
 };
 
 
@@ -63,6 +65,8 @@ struct InitArgs {
     int order, xper, yper;
 };
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st);
+// per-node mu (compact FP64) -> compute-type plane in the u* layout (zero padding)
+cudaError_t launch_mu_plane(int storage, const double *mu, void *plane, const Layout &L, cudaStream_t st);
 
 struct ReadArgs {
     const void *f;      // current post-collision populations
@@ -87,6 +91,69 @@ struct DiagArgs {
 };
 int diag_blocks(const Layout &L);
 cudaError_t launch_diag(int storage, const DiagArgs &a, cudaStream_t st);
+
+// lbm_adjoint_kernels.cu (see there for the equations)
+template <typename T>
+struct AdjArgs {
+    const void *fin;    // f*^n, ghosts filled
+    const void *ain;    // a^{n+1}
+    void *aout;         // a^n (interior and ghost cells; k_adj_fold completes it)
+    const T *mufield;   // u* plane layout
+    const T *ubar;      // dL/du*, two planes, u* plane layout
+    double *gmu;        // dL/dmu accumulator, u* plane layout
+    Layout L;
+    T one_m_omega, wq, wi2c, dtT;  // 1 - w, w/4, w/(2c), dt
+    T hdtb1, hdtb2, lam_ratio;
+    double wi2c_d;
+};
+template <typename T>
+struct FoldArgs {
+    const void *fin;
+    void *aout;
+    const T *mufield;
+    double *gmu;
+    Layout L;
+    int kind[4];
+    double value[4][2], g[4];  // edge data of the ghosts of f*^n: value * g * profile
+    const double *profile[4];
+    T hdtb1, hdtb2, lam_ratio;
+    int count;                 // boundary ring nodes
+};
+struct RecordArgs {
+    const void *f;
+    const double *ustar;
+    const int *sens;  // (x, y) pairs
+    double *out;      // 2 per sensor
+    int nsens;
+    Layout L;
+    double dt, b1, b2;
+};
+template <typename T>
+struct InjectArgs {
+    void *aout;
+    T *ubar;
+    const int *sens;
+    const double *rec, *tgt;  // 2 per sensor, this record
+    int nsens;
+    Layout L;
+    double dt;
+};
+struct AdjInitArgs {
+    InitArgs ia;        // the forward's init arguments (U0, material, edges' periodicity)
+    const void *a0;     // a^0
+    const void *ubar;   // compute-type planes
+    double *gmu;        // plane
+    double *gv0;        // 2N compact (output)
+    double *ghat;       // 4N compact scratch
+};
+cudaError_t launch_adj(int storage, int law, const void *args, int grid, cudaStream_t st);
+int adj_blocks_per_sm(int storage, int law);
+int adj_vec_for(int storage);  // nodes per lane of the adjoint kernel
+cudaError_t launch_adj_fold(int storage, int law, const void *args, cudaStream_t st);
+cudaError_t launch_adj_record(int storage, const RecordArgs &a, cudaStream_t st);
+cudaError_t launch_adj_inject(int storage, const void *args, cudaStream_t st);
+cudaError_t launch_adj_init(int storage, const AdjInitArgs &a, cudaStream_t st);
+cudaError_t launch_plane_to_compact(const double *plane, double *out, const Layout &L, cudaStream_t st);
 
 // lbm_api.cu: message returned by lbm_last_error(NULL) on this host thread
 void set_thread_error(const std::string &msg);

@@ -209,6 +209,8 @@ extern "C" lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t
     a.m.law = law;
     a.m.lam = params[0];
     a.m.mu = params[1];
+    a.m.mufield = nullptr;
+    a.m.lam_ratio = 0.0;
     a.dx = dx;
     a.partial = partial;
     a.out = out_dev;

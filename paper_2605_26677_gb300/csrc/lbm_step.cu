@@ -15,7 +15,7 @@
 #include "lbm_step_core.cuh"
 
 namespace tlv {
-template <typename S, int LAW, int VEC, bool FUSE>
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
 {
     const int lane = threadIdx.x & 31;
@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
     unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE>(a, task, lane, flags);
+    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
     double val[2];
     edge_value(E, s, a.g[e], val);
     unsigned flags = 0;
-    edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, (T)a.m.lam, (T)a.m.mu, out, flags);
+    double lam, mu;
+    mat_at(a.m, (long long)yb * a.L.nx + xb, lam, mu);
+    edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, (T)lam, (T)mu, out, flags);
     if (flags) atomicOr(a.status, (int)flags);
 #pragma unroll
     for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = to_store<S>(out[k]);
@@ -188,6 +190,8 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
     const double Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? -1.0 : 1.0;
     int x0, y0;
     edge_node(a.L, e, 0, s, x0, y0);
+    double lam, mu;
+    mat_at(a.m, (long long)y0 * a.L.nx + x0, lam, mu);
     double U0[6];
     node_state(v, x0, y0, a.hdtb1, a.hdtb2, U0);
     if (a.fb_mode == FB_EXTRAP2) {
@@ -209,7 +213,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
     const double tmax = fmax(fabs(Tb[0]), fabs(Tb[1]));
     const double tol = 1e-13 * (tmax > 1.0 ? tmax : 1.0);
     double P[4], dJ, r[2];
-    piola_law(a.m.law, Gb, a.m.lam, a.m.mu, P, dJ);
+    piola_law(a.m.law, Gb, lam, mu, P, dJ);
     r[0] = Na * P[0 * 2 + an] - Tb[0];
     r[1] = Na * P[1 * 2 + an] - Tb[1];
     for (int it = 0; it < 20; ++it) {
@@ -219,7 +223,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
         for (int k = 0; k < 2; ++k) {
             double dF[4] = {0.0, 0.0, 0.0, 0.0}, dP[4];
             dF[k * 2 + an] = 1.0;
-            tangent_jvp(a.m.law, F, dF, a.m.lam, a.m.mu, dP);
+            tangent_jvp(a.m.law, F, dF, lam, mu, dP);
             Jac[0][k] = Na * dP[0 * 2 + an];
             Jac[1][k] = Na * dP[1 * 2 + an];
         }
@@ -236,7 +240,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
             const double Jt = (1.0 + Gt[0]) * (1.0 + Gt[3]) - Gt[1] * Gt[2];
             if (Jt > 0.0) {
                 double Pt[4], dJt, rt[2];
-                piola_law(a.m.law, Gt, a.m.lam, a.m.mu, Pt, dJt);
+                piola_law(a.m.law, Gt, lam, mu, Pt, dJt);
                 rt[0] = Na * Pt[0 * 2 + an] - Tb[0];
                 rt[1] = Na * Pt[1 * 2 + an] - Tb[1];
                 if (hypot(rt[0], rt[1]) < rn) {
@@ -315,6 +319,18 @@ __global__ void __launch_bounds__(128) k_edges(const EdgeArgs a)
 template <typename S, int LAW>
 static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
 {
+    if (a.mufield) {
+        // per-node material: FP64 and FP32 storage
+        if constexpr (sizeof(S) == 2) {
+            return cudaErrorNotSupported;
+        } else {
+            if (fuse)
+                k_step<S, LAW, 16 / sizeof(S), true, true><<<grid, 128, 0, st>>>(a);
+            else
+                k_step<S, LAW, 16 / sizeof(S), false, true><<<grid, 128, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(S) == 2) {
         if (fuse)
             k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);

@@ -49,8 +49,8 @@ __device__ __forceinline__ void state_from_fstar(const T f0[6], const T f1[6], c
 // Eq. (12) equilibrium and Eq. (14) collision, in place on the four streamed
 // populations f[q][k] (offsets). Returns the velocity v^n.
 template <int LAW, typename T>
-__device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, bool real, unsigned &flags, T &v1,
-                                             T &v2)
+__device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, T lam, T mu, bool real,
+                                             unsigned &flags, T &v1, T &v2)
 {
     T U[6];
 #pragma unroll
@@ -58,7 +58,7 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, bo
     U[0] += a.hdtb1;
     U[1] += a.hdtb2;
     T P11, P12, P21, P22, dJ;
-    piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], a.lam, a.mu, P11, P12, P21, P22, dJ);
+    piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], lam, mu, P11, P12, P21, P22, dJ);
     if (real) {
         if (!(dJ > T(-1))) flags |= ST_BAD_J;
         if (!(fabs(U[0]) + fabs(U[1]) + fabs(dJ) < T(INFINITY))) flags |= ST_NONFINITE;
@@ -87,8 +87,8 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, bo
 // column (plane 2, x = nx), with the edge data of the step that will pull
 // these values.
 template <int LAW, typename S, typename T>
-__device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, S *fout,
-                                            unsigned &flags)
+__device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, T lam, T mu,
+                                            S *fout, unsigned &flags)
 {
     const int nx = a.L.nx, ny = a.L.ny;
     auto put = [&](int e, int gx, int gy, const T val[6]) {
@@ -102,7 +102,7 @@ __device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const
         state_from_fstar(f[0], f[1], f[2], f[3], a.hdtb1, a.hdtb2, U);
         const double g = (a.gdev ? a.gdev[e] : a.g[e]) * (a.profile[e] ? a.profile[e][s] : 1.0);
         const double val[2] = {a.value[e][0] * g, a.value[e][1] * g};
-        edge_ghost<LAW, T>(e, a.kind[e], f[edge_dout(e)], U, val, a.c, a.lam, a.mu, out, flags);
+        edge_ghost<LAW, T>(e, a.kind[e], f[edge_dout(e)], U, val, a.c, lam, mu, out, flags);
         put(e, gx, gy, out);
     };
     if (a.kind[EDGE_BOTTOM] == BC_PERIODIC) {
@@ -136,7 +136,7 @@ __device__ __forceinline__ void task_coords(int task, int nseg, int &y, int &seg
 // back by the same thread), so the edge work never adds to the register peak
 // of the streaming loop, and it sees exactly the values the ghost-refresh
 // kernel would read.
-template <int LAW, typename S, int VEC>
+template <int LAW, typename S, int VEC, bool MATF = false>
 __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> &a, S *fout, long long row, int x0,
                                             int y, unsigned &flags)
 {
@@ -154,13 +154,18 @@ __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> 
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(fout[(q * 6 + k) * a.L.plane + row + e]);
-        node_ghosts<LAW, S, T>(fq, x, y, a, fout, flags);
+        T lam = a.lam, mu = a.mu;
+        if (MATF) {
+            mu = a.mufield[(long long)y * a.L.upitch + x];
+            lam = a.lam_ratio * mu;
+        }
+        node_ghosts<LAW, S, T>(fq, x, y, a, lam, mu, fout, flags);
     }
 }
 
 // FP64 and FP32 storage: VEC nodes per lane as 16-byte vectors, unpacked.
 // One (row, segment) task of lattice `a`, executed by a whole warp.
-template <typename S, int LAW, int VEC, bool FUSE>
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
 __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a, int task, int lane,
                                           unsigned &flags)
 {
@@ -206,6 +211,14 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
                 f[3][k][e] = ld_r(c3.v[e]);                                // from y + 1
             }
         }
+        T muv[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) muv[e] = a.mu;
+        if (MATF && act) {
+            const Pack<T, VEC> m = *reinterpret_cast<const Pack<T, VEC> *>(a.mufield + (long long)y * a.L.upitch + x0);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) muv[e] = m.v[e];
+        }
         T vel[2][VEC];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
@@ -214,7 +227,8 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) fq[q][k] = f[q][k][e];
-            collide_node<LAW, T>(fq, a, x0 + e < nx, flags, vel[0][e], vel[1][e]);
+            collide_node<LAW, T>(fq, a, MATF ? a.lam_ratio * muv[e] : a.lam, muv[e], x0 + e < nx, flags, vel[0][e],
+                                 vel[1][e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -249,7 +263,7 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
                 for (int e = 0; e < VEC; ++e) u.v[e] += a.dt * (double)vel[c][e];
                 *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
             }
-            if (FUSE) lane_ghosts<LAW, S, VEC>(a, fout, row, x0, y, flags);
+            if (FUSE) lane_ghosts<LAW, S, VEC, MATF>(a, fout, row, x0, y, flags);
         }
     }
 }
@@ -372,7 +386,7 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) fq[q][k] = unpack16(w[q][k].w[e >> 1], e & 1, S());
-            collide_node<LAW, float>(fq, a, x0 + e < nx, flags, vel[0][e], vel[1][e]);
+            collide_node<LAW, float>(fq, a, a.lam, a.mu, x0 + e < nx, flags, vel[0][e], vel[1][e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll

@@ -26,13 +26,16 @@ LBM_T_CONST, LBM_T_LINEAR_RAMP, LBM_T_SIN2_RAMP, LBM_T_SIN_PULSE, LBM_T_RICKER =
 LBM_FB_NODE, LBM_FB_EXTRAP2 = range(2)
 
 # every symbol include/lbm.h declares
-EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "lbm_set_body_force",
+EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "lbm_set_material_field",
+           "lbm_set_body_force",
            "lbm_set_boundary", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
            "lbm_read_state", "lbm_read_state_device", "lbm_read_displacement", "lbm_read_displacement_device",
            "lbm_read_cauchy", "lbm_diagnostics", "lbm_save", "lbm_load", "lbm_info", "lbm_profile",
            "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_size_class",
-           "lbm_batch_get_tiles", "lbm_batch_set_tile", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_info"]
+           "lbm_batch_get_tiles", "lbm_batch_set_tile", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_info",
+           "lbm_adjoint_create", "lbm_adjoint_destroy", "lbm_adjoint_last_error", "lbm_adjoint_set_loss",
+           "lbm_adjoint_forward", "lbm_adjoint_backward", "lbm_adjoint_info"]
 LBM_BATCH_MAX_MEMBERS = 4096
 LBM_BATCH_CLASSES = 5
 
@@ -72,6 +75,7 @@ _lib.lbm_destroy.restype = None
 _lib.lbm_last_error.argtypes = [_ctx]
 _lib.lbm_last_error.restype = C.c_char_p
 _lib.lbm_set_material.argtypes = [_ctx, C.c_int32, _dp, C.c_int32]
+_lib.lbm_set_material_field.argtypes = [_ctx, C.c_int32, _dp, C.c_double]
 _lib.lbm_set_body_force.argtypes = [_ctx, C.c_double, C.c_double]
 _lib.lbm_set_boundary.argtypes = [_ctx, C.c_int32, C.c_int32, _dp, C.c_int32, _dp, _dp]
 _lib.lbm_init.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
@@ -109,6 +113,17 @@ _lib.lbm_batch_set_tile.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
 _lib.lbm_batch_tune.argtypes = [C.c_void_p, C.c_int32, _dp]
 _lib.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _ip]
 _lib.lbm_batch_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _ip, _ip]
+
+
+_lib.lbm_adjoint_create.argtypes = [_ctx, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]
+_lib.lbm_adjoint_destroy.argtypes = [C.c_void_p]
+_lib.lbm_adjoint_destroy.restype = None
+_lib.lbm_adjoint_last_error.argtypes = [C.c_void_p]
+_lib.lbm_adjoint_last_error.restype = C.c_char_p
+_lib.lbm_adjoint_set_loss.argtypes = [C.c_void_p, C.c_int32, _ip, C.c_int32, _ip, _dp]
+_lib.lbm_adjoint_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _dp]
+_lib.lbm_adjoint_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.lbm_adjoint_info.argtypes = [C.c_void_p, _ip, C.POINTER(C.c_int64), _dp, _dp]
 
 
 def library():
@@ -191,6 +206,14 @@ def lbm_last_error(ctx=None):
 def lbm_set_material(ctx, law, params):
     p = np.asarray(params, dtype=np.float64)
     _check(ctx, _lib.lbm_set_material(ctx, law, p.ctypes.data_as(_dp), len(p)))
+
+
+def lbm_set_material_field(ctx, law, mu, lam_ratio):
+    """mu: (ny, nx) float64 host array; lambda = lam_ratio * mu per node."""
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    if m.size != ctx.nx * ctx.ny:
+        raise ValueError("mu needs one value per node")
+    _check(ctx, _lib.lbm_set_material_field(ctx, law, m.ctypes.data_as(_dp), float(lam_ratio)))
 
 
 def lbm_set_body_force(ctx, b1, b2):
@@ -395,6 +418,71 @@ def lbm_batch_info(b):
     n, l, g = C.c_int64(), C.c_int32(), C.c_int32()
     _bcheck(b, _lib.lbm_batch_info(b, C.byref(n), C.byref(l), C.byref(g)))
     return {"nodes": n.value, "launches_per_step": l.value, "graphs": g.value}
+
+
+# ---------------------------------------------------------------- adjoint
+class Adjoint:
+    """Opaque adjoint handle returned by lbm_adjoint_create; keeps its
+    context referenced."""
+
+    def __init__(self, handle, ctx, nsteps):
+        self._as_parameter_ = handle
+        self.ctx = ctx
+        self.nsteps = nsteps
+
+
+def _acheck(a, status):
+    if status != LBM_OK:
+        msg = _lib.lbm_adjoint_last_error(a)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+def lbm_adjoint_create(ctx, nsteps, checkpoint_every=0):
+    h = C.c_void_p()
+    _acheck(None, _lib.lbm_adjoint_create(ctx, int(nsteps), int(checkpoint_every), C.byref(h)))
+    return Adjoint(h, ctx, nsteps)
+
+
+def lbm_adjoint_destroy(a):
+    if a is not None and a._as_parameter_ is not None:
+        _lib.lbm_adjoint_destroy(a)
+        a._as_parameter_ = None
+
+
+def lbm_adjoint_last_error(a=None):
+    m = _lib.lbm_adjoint_last_error(a)
+    return m.decode() if m else ""
+
+
+def lbm_adjoint_set_loss(a, sens_xy, rec_steps, target):
+    """sens_xy: (nsens, 2) node (x, y); rec_steps: (nrec,); target: (nrec, nsens, 2)."""
+    s = np.ascontiguousarray(sens_xy, dtype=np.int32).reshape(-1, 2)
+    r = np.ascontiguousarray(rec_steps, dtype=np.int32).ravel()
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    if t.size != len(r) * len(s) * 2:
+        raise ValueError("target needs (nrec, nsens, 2) values")
+    _acheck(a, _lib.lbm_adjoint_set_loss(a, len(s), s.ctypes.data_as(_ip), len(r), r.ctypes.data_as(_ip),
+                                         t.ctypes.data_as(_dp)))
+
+
+def lbm_adjoint_forward(a, U0_dev, order=2):
+    """U0_dev: (6, ny, nx) float64 CUDA tensor. Returns the loss."""
+    L = C.c_double()
+    _acheck(a, _lib.lbm_adjoint_forward(a, _dev(U0_dev, 6 * a.ctx.nx * a.ctx.ny), int(order), C.byref(L)))
+    return L.value
+
+
+def lbm_adjoint_backward(a, g_mu_dev, g_v0_dev):
+    """g_mu_dev: (ny, nx), g_v0_dev: (2, ny, nx) float64 CUDA tensors (written)."""
+    N = a.ctx.nx * a.ctx.ny
+    _acheck(a, _lib.lbm_adjoint_backward(a, _dev(g_mu_dev, N), _dev(g_v0_dev, 2 * N)))
+
+
+def lbm_adjoint_info(a):
+    k, n, f, b = C.c_int32(), C.c_int64(), C.c_double(), C.c_double()
+    _acheck(a, _lib.lbm_adjoint_info(a, C.byref(k), C.byref(n), C.byref(f), C.byref(b)))
+    return {"checkpoint_every": k.value, "stored_states": n.value, "forward_ms": f.value, "backward_ms": b.value}
 
 
 # ---------------------------------------------------------------- helper

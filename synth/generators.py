@@ -14,7 +14,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["splitmix64_uniform", "Workload", "shear_wave_64", "clamped_specimen",
-           "fourier_periodic", "specimen_batch", "rest_state", "WORKLOADS"]
+           "fourier_periodic", "specimen_batch", "adjoint_specimen", "gaussian_random_field",
+           "standard_normals", "rest_state", "WORKLOADS"]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -206,7 +207,71 @@ def specimen_batch(n=256, seed=2, side_min=64, side_max=1024, storage="f32", ste
     return out
 
 
+def standard_normals(seed: int, n: int) -> np.ndarray:
+    """n standard normals by the Box-Muller transform of SplitMix64 pairs."""
+    u = splitmix64_uniform(seed, 2 * n).reshape(n, 2)
+    return np.sqrt(-2.0 * np.log(1.0 - u[:, 0])) * np.cos(2.0 * np.pi * u[:, 1])
+
+
+def gaussian_random_field(nx, ny, corr, seed):
+    """Zero-mean, unit-variance periodic Gaussian random field on the node
+    grid with covariance exp(-r^2 / (2 corr^2)) (r in nodes): seeded white
+    noise filtered by exp(-|k|^2 corr^2 / 4) in Fourier space, normalised to
+    unit sample variance."""
+    w = standard_normals(seed, nx * ny).reshape(ny, nx)
+    kx = 2.0 * np.pi * np.fft.fftfreq(nx)
+    ky = 2.0 * np.pi * np.fft.fftfreq(ny)
+    filt = np.exp(-(ky[:, None] ** 2 + kx[None, :] ** 2) * corr ** 2 / 4.0)
+    g = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
+    g -= g.mean()
+    return g / g.std()
+
+
+def _adjoint_fields(w: Workload):
+    """Gaussian velocity pulse v = A (cos th, sin th) exp(-|X - X_c|^2 / (2 r^2))
+    at X_c = (0.3 nx, 0.5 ny) nodes, r = nx / 32 nodes, A = 0.01; F = I."""
+    nx, ny = w.nx, w.ny
+    p = w.params
+    X = np.arange(nx) + 0.5
+    Y = np.arange(ny) + 0.5
+    r2 = (X[None, :] - 0.3 * nx) ** 2 + (Y[:, None] - 0.5 * ny) ** 2
+    prof = p["amp"] * np.exp(-r2 / (2.0 * p["radius"] ** 2))
+    U0 = rest_state(nx, ny)
+    U0[0] = np.cos(p["theta"]) * prof
+    U0[1] = np.sin(p["theta"]) * prof
+    return U0, np.zeros((2, ny, nx))
+
+
+def adjoint_specimen(n=1024, seed=3, steps=2000, corr=None, sigma=0.3, nsens=64, record_every=20,
+                     storage="f32", omega=1.95):
+    """Clamped-left square specimen (traction-free right, bottom and top
+    edges) with a log-normal shear-modulus field mu = exp(sigma g), g a
+    Gaussian random field of correlation length corr nodes (n / 16 by
+    default, 64 at n = 1024) drawn with `seed`; lambda = 2 mu; NH; a Gaussian
+    velocity pulse (direction from draw 0 of stream seed + 1); c = max(5,
+    3 c_P,max), c_P,max = sqrt(4 max mu). Sensors: nsens nodes on the right
+    edge at rows (j + 1/2) n / nsens; records every record_every steps.
+    Target displacements d = 1e-3 (2 U - 1) from stream seed + 2 (a synthetic
+    observation), shaped (records, sensors, 2). The field, sensors, records
+    and targets are in params."""
+    corr = n / 16.0 if corr is None else corr
+    mu = np.exp(sigma * gaussian_random_field(n, n, corr, seed))
+    c = max(5.0, 3.0 * np.sqrt(4.0 * mu.max()))
+    sens = np.array([[n - 1, int((j + 0.5) * n / nsens)] for j in range(nsens)], dtype=np.int32)
+    rec = np.arange(record_every, steps + 1, record_every, dtype=np.int32)
+    tgt = 1e-3 * (2.0 * splitmix64_uniform(seed + 2, len(rec) * nsens * 2) - 1.0)
+    theta = 2.0 * np.pi * splitmix64_uniform(seed + 1, 1)[0]
+    edges = [Edge("velocity"), Edge("traction"), Edge("traction"), Edge("traction")]
+    return Workload("adjoint_specimen", n, n, lam=2.0 * float(mu.mean()), mu=float(mu.mean()), c=c, omega=omega,
+                    steps=steps, storage=storage, edges=edges, seed=seed,
+                    params={"mu": mu, "lam_ratio": 2.0, "sensors": sens, "records": rec,
+                            "target": tgt.reshape(len(rec), nsens, 2), "theta": theta, "amp": 0.01,
+                            "radius": n / 32.0},
+                    note="clamped-left specimen, log-normal mu(X), velocity pulse, right-edge sensors")
+
+
 _FIELD_BUILDERS["shear_wave"] = _shear_wave_fields
+_FIELD_BUILDERS["adjoint_specimen"] = _adjoint_fields
 _FIELD_BUILDERS["batch_member"] = _batch_member_fields
 _FIELD_BUILDERS["clamped_specimen"] = _rest_fields
 _FIELD_BUILDERS["fourier_periodic"] = _fourier_fields
@@ -216,4 +281,5 @@ WORKLOADS = {
     "clamped_specimen": clamped_specimen,
     "fourier_periodic": fourier_periodic,
     "specimen_batch": specimen_batch,
+    "adjoint_specimen": adjoint_specimen,
 }

@@ -84,3 +84,15 @@ def test_batch_create_rejects_bad_arguments_before_touching_the_device(lbm):
     assert lib.lbm_batch_create(arr, lbm.LBM_BATCH_MAX_MEMBERS + 1, C.byref(out)) == lbm.LBM_ERR_ARG
     assert out.value is None
     assert lib.lbm_batch_step(None, 1, 0, None) == lbm.LBM_ERR_ARG
+
+
+def test_adjoint_create_rejects_bad_arguments_before_touching_the_device(lbm):
+    import ctypes as C
+
+    lib = lbm.library()
+    out = C.c_void_p()
+    assert lib.lbm_adjoint_create(None, 10, 0, C.byref(out)) == lbm.LBM_ERR_ARG
+    assert lib.lbm_adjoint_create(None, 10, 0, None) == lbm.LBM_ERR_ARG
+    assert b"NULL" in lib.lbm_adjoint_last_error(None)
+    assert lib.lbm_adjoint_set_loss(None, 1, None, 1, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_adjoint_backward(None, None, None) == lbm.LBM_ERR_ARG
