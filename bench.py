@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-forms", action="store_true", help="skip the FP64 and 8192^2 side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    p.add_argument("--form", choices=["batch", "adjoint"], default=None,
+                   help="run only this side measurement and print its JSON (profiling); not a bench line")
+    p.add_argument("--form-steps", type=int, default=None, help="steps of the --form run")
     return p.parse_args()
 
 
@@ -181,7 +184,7 @@ def recorded_traffic():
     except Exception:
         return None
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_device.cuh", "lbm_edges.cuh"):
+    for f in ("lbm_step.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_edges.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2605_26677_gb300", "csrc", f), "rb").read())
     if kv.get("source_sha256") != h.hexdigest():
         return None
@@ -374,7 +377,7 @@ def batch_form(lbm, torch, peak, steps, graph_steps=20):
                     "U(1,4), clamped left, other edges clamped or traction-free; GB/s over the whole step"}
 
 
-def adjoint_form(lbm, torch, steps=2000):
+def adjoint_form(lbm, torch, steps=2000, all_states=True):
     """Gradient of the right-edge sensor misfit with respect to mu(X) and v0
     on the 1024^2 differentiation workload (FP32, 2000 steps, sqrt(N)
     checkpoints): device time of the forward (with checkpoints and sensor
@@ -387,7 +390,7 @@ def adjoint_form(lbm, torch, steps=2000):
     U0, _ = w.fields()
     U0d = torch.from_numpy(U0).cuda()
     out = {}
-    for name, K in (("sqrtN", 0), ("all_states", 1)):
+    for name, K in (("sqrtN", 0), ("all_states", 1))[: 2 if all_states else 1]:
         L = lbm.Lattice(w.nx, w.ny, dx=w.dx, c=w.c, omega=w.omega, storage=lbm.LBM_STORE_F32)
         lbm.lbm_set_material_field(L.ctx, lbm.LBM_LAW_NH, p["mu"], p["lam_ratio"])
         kinds = {"velocity": lbm.LBM_BC_VELOCITY, "traction": lbm.LBM_BC_TRACTION}
@@ -469,7 +472,19 @@ def run_reference(args, rank, ws):
 def main():
     args = parse()
     rank, ws, dist = dist_setup(args)
-    if args.impl == "reference":
+    if args.form is not None:
+        import torch
+
+        from paper_2605_26677_gb300 import build
+
+        build.build()
+        from paper_2605_26677_gb300 import lbm
+
+        if args.form == "batch":
+            line = {"form": "batch", **batch_form(lbm, torch, peaks()[0], args.form_steps or 200)}
+        else:
+            line = {"form": "adjoint", **adjoint_form(lbm, torch, args.form_steps or 2000, all_states=False)}
+    elif args.impl == "reference":
         line = run_reference(args, rank, ws)
     else:
         line = run_ours(args, rank, ws, dist)
