@@ -184,7 +184,7 @@ def recorded_traffic():
     except Exception:
         return None
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_edges.cuh"):
+    for f in ("lbm_step_kernels.cuh", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_edges.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2605_26677_gb300", "csrc", f), "rb").read())
     if kv.get("source_sha256") != h.hexdigest():
         return None

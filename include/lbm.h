@@ -126,10 +126,17 @@ void lbm_destroy(lbm_ctx *ctx);
  * lbm_diagnostics_state_noalloc). Valid until the next call on ctx. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A). Needed
- * before lbm_init; set later, it applies from the next step on (the lattice
- * speed is not checked again). Waits for the context's queued work. Replaces
- * a material field. LBM_ERR_UNSUPPORTED for MR, YEOH, GENT. */
+/* Hyperelastic closure and its parameters (Sec. 2.3, Appendix A):
+ *   SVK, NH, LOGNH: {lambda, mu}          (mu > 0)
+ *   MR:   {lambda, c10, c01}              (c10, c01 >= 0, c10 + c01 > 0)
+ *   YEOH: {lambda, c1, c2, c3}            (c1 > 0)
+ *   GENT: {lambda, mu, Jm}                (mu > 0, Jm > 0)
+ * with lambda + 2 mu_0 > 0 for the small-strain shear modulus mu_0 (2 (c10 +
+ * c01) for MR, 2 c1 for Yeoh); LBM_ERR_ARG otherwise. The MR, Yeoh and Gent
+ * closures use the isochoric invariants of the plane-strain C (C33 = 1).
+ * Needed before lbm_init; set later, it applies from the next step on (the
+ * lattice speed is not checked again). Waits for the context's queued work.
+ * Replaces a material field. */
 lbm_status lbm_set_material(lbm_ctx *ctx, int32_t law, const double *params, int32_t nparams);
 
 /* Per-node material (the paper's closures are pointwise, so Eq. (14) takes
@@ -228,8 +235,9 @@ double lbm_bytes_per_node_update(const lbm_ctx *ctx);
  * allocation. It reduces the caller's FP64 state U_dev (device, 6N,
  * component-major v1, v2, F11, F12, F21, F22; e.g. from
  * lbm_read_state_device) into the caller's out_dev (device, 10 doubles, the
- * layout of lbm_diagnostics) for closure `law` (SVK, NH, LOGNH) with params
- * {lambda, mu} and spacing dx, on `stream` of `device`, without waiting.
+ * layout of lbm_diagnostics) for closure `law` with its params (as
+ * lbm_set_material lists them) and spacing dx, on `stream` of `device`,
+ * without waiting.
  * Its block partials live in one fixed 1.25 MiB array in the library's device
  * memory (held on every GPU that loads the library until the process exits),
  * so a call takes at most 67,108,864 nodes (8192^2) and returns LBM_ERR_ARG

@@ -111,9 +111,9 @@ int ring_count(const Layout &L)
     return rows * L.nx + (L.ny > 2 ? (L.ny - 2) * cols : 0);
 }
 
-// the ghosts of f*^n hold edge data at t^n + dt/2
+// the traction ghosts of f*^n carry the converged F^b of the forward
 template <typename T>
-FoldArgs<T> fold_args(const lbm_adjoint *a, const void *fin, void *aout, long long n)
+FoldArgs<T> fold_args(const lbm_adjoint *a, const void *fin, void *aout)
 {
     const lbm_ctx *c = a->c;
     FoldArgs<T> r;
@@ -122,15 +122,7 @@ FoldArgs<T> fold_args(const lbm_adjoint *a, const void *fin, void *aout, long lo
     r.mufield = static_cast<const T *>(c->d_muplane);
     r.gmu = a->gmu;
     r.L = c->L;
-    for (int e = 0; e < 4; ++e) {
-        r.kind[e] = c->edge[e].kind;
-        r.value[e][0] = c->edge[e].value[0];
-        r.value[e][1] = c->edge[e].value[1];
-        r.g[e] = ctx_time_factor(c, e, n - 1);
-        r.profile[e] = c->edge[e].profile;
-    }
-    r.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
-    r.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
+    for (int e = 0; e < 4; ++e) r.kind[e] = c->edge[e].kind;
     r.lam_ratio = (T)c->m.lam_ratio;
     r.count = ring_count(c->L);
     return r;
@@ -192,18 +184,18 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
     return LBM_OK;
 }
 
-lbm_status adjoint_step(lbm_adjoint *a, const void *fin, const void *ain, void *aout, long long n, int grid)
+lbm_status adjoint_step(lbm_adjoint *a, const void *fin, const void *ain, void *aout, int grid)
 {
     lbm_ctx *c = a->c;
     if (fp64(a)) {
         const AdjArgs<double> r = adj_args<double>(a, fin, ain, aout);
         AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
-        const FoldArgs<double> fr = fold_args<double>(a, fin, aout, n);
+        const FoldArgs<double> fr = fold_args<double>(a, fin, aout);
         AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
     } else {
         const AdjArgs<float> r = adj_args<float>(a, fin, ain, aout);
         AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
-        const FoldArgs<float> fr = fold_args<float>(a, fin, aout, n);
+        const FoldArgs<float> fr = fold_args<float>(a, fin, aout);
         AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
     }
     return LBM_OK;
@@ -430,7 +422,7 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
             if (s != LBM_OK) return s;
         }
         for (long long n = s1 - 1; n >= s0; --n) {
-            s = adjoint_step(a, state(n), a->A[cur], a->A[cur ^ 1], n, grid);
+            s = adjoint_step(a, state(n), a->A[cur], a->A[cur ^ 1], grid);
             if (s != LBM_OK) return s;
             cur ^= 1;
             if (a->rec_at[(size_t)n] >= 0) {

@@ -21,8 +21,9 @@
 // domain land in the ghost cells; k_adj_fold then applies the transposed
 // edge rules there (velocity: a^n_{-d} = D h_d; traction: the same plus the
 // implicit-function-theorem derivative of the Newton solve for F^b, which
-// depends on the boundary node's tangential column and mu; periodic: the
-// ghost goes back to the node it was copied from).
+// depends on the boundary node's tangential column and mu, evaluated at the
+// F^b the forward stored in the ghost cell; periodic: the ghost goes back to
+// the node it was copied from).
 #include "lbm_init_core.cuh"
 #include "lbm_step_core.cuh"
 
@@ -118,10 +119,11 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
             }
             const T G[4] = {U[2][e], U[3][e], U[4][e], U[5][e]};
             const T M[4] = {bX[0], bY[0], bX[1], bY[1]};  // cotangent of (P11, P12, P21, P22)
-            const T m = mu.v[e], lam = a.lam_ratio * m;
+            const LawP<T> mp{a.lam_ratio * mu.v[e], mu.v[e], T(0), T(0)};
+            const LawP<T> unit{a.lam_ratio, T(1), T(0), T(0)};  // d(lambda, mu)/dmu
             T CM[4], Pm[4], dJ;
-            jvp_ofs<LAW, T>(G, M, lam, m, CM);
-            piola_ofs<LAW, T>(G[0], G[1], G[2], G[3], a.lam_ratio, T(1), Pm[0], Pm[1], Pm[2], Pm[3], dJ);
+            jvp_ofs<LAW, T>(G, M, mp, CM);
+            piola_ofs<LAW, T>(G[0], G[1], G[2], G[3], unit, Pm[0], Pm[1], Pm[2], Pm[3], dJ);
             T g[6];
             g[0] = a.wq * Sa[0] - a.wi2c * (bX[2] + bY[3]) + a.dtT * ub0.v[e];
             g[1] = a.wq * Sa[1] - a.wi2c * (bX[4] + bY[5]) + a.dtT * ub1.v[e];
@@ -233,6 +235,10 @@ __device__ __forceinline__ void ghost_cell(int e, int s, int nx, int ny, int &gx
     }
 }
 
+// One thread per boundary-ring node. Every value the node's edges need is
+// loaded first, the transposed rules are applied in registers, and the node's
+// cells are stored last, so the loads are independent and issue together
+// (a thread walks at most four edges; its destination planes are distinct).
 template <typename S, int LAW>
 __global__ void __launch_bounds__(128) k_adj_fold(const FoldArgs<typename Prec<S>::R> a)
 {
@@ -242,63 +248,89 @@ __global__ void __launch_bounds__(128) k_adj_fold(const FoldArgs<typename Prec<S
     const int nx = a.L.nx, ny = a.L.ny;
     int x, y;
     ring_node(t, nx, ny, x, y);
-    const S *fin = static_cast<const S *>(a.fin);
-    S *aout = static_cast<S *>(a.aout);
+    const S *__restrict__ fin = static_cast<const S *>(a.fin);
+    S *__restrict__ aout = static_cast<S *>(a.aout);
     auto idx = [&](int q, int k, int xx, int yy) {
         return (long long)(q * 6 + k) * a.L.plane + (long long)(yy + 1) * a.L.pitch + a.L.xoff + xx;
     };
-    T UG[4] = {T(0), T(0), T(0), T(0)};
-    double gm = 0.0;
+    bool on[4];
+    on[EDGE_LEFT] = x == 0;
+    on[EDGE_RIGHT] = x == nx - 1;
+    on[EDGE_BOTTOM] = y == 0;
+    on[EDGE_TOP] = y == ny - 1;
     bool traction = false;
+    for (int e = 0; e < 4; ++e) traction = traction || (on[e] && a.kind[e] == BC_TRACTION);
+
+    // loads
+    T src[4][6];       // per edge: the ghost value it takes its cotangent from
+    T gb[4][4];        // per traction edge: the forward's G^b
+    T cur[4][4];       // the node's F-components in every plane (for the broadcast)
+    int dest[4];       // destination plane per edge, -1 if none
     for (int e = 0; e < 4; ++e) {
-        const bool on = (e == EDGE_LEFT) ? x == 0 : (e == EDGE_RIGHT) ? x == nx - 1 : (e == EDGE_BOTTOM) ? y == 0
-                                                                                                        : y == ny - 1;
-        if (!on) continue;
+        dest[e] = -1;
+        if (!on[e]) continue;
         const int s = (e <= EDGE_RIGHT) ? y : x;
         int gx, gy;
         if (a.kind[e] == BC_PERIODIC) {
             // this node's outgoing population was copied into the opposite
             // edge's ghost cell; its cotangent comes back from there
             const int o = e ^ 1;  // LEFT <-> RIGHT, BOTTOM <-> TOP
-            const int p = edge_dmiss(o);
+            dest[e] = edge_dmiss(o);
             ghost_cell(o, s, nx, ny, gx, gy);
-            for (int k = 0; k < 6; ++k) aout[idx(p, k, x, y)] = aout[idx(p, k, gx, gy)];
+            for (int k = 0; k < 6; ++k) src[e][k] = ld_r(aout[idx(dest[e], k, gx, gy)]);
             continue;
         }
         const int d = edge_dmiss(e), md = edge_dout(e);
+        dest[e] = md;
         ghost_cell(e, s, nx, ny, gx, gy);
-        T cot[6];
-        for (int k = 0; k < 6; ++k) cot[k] = ld_r(aout[idx(d, k, gx, gy)]);
+        for (int k = 0; k < 6; ++k) src[e][k] = ld_r(aout[idx(d, k, gx, gy)]);
+        if (a.kind[e] == BC_TRACTION)
+            // the forward stored ghost = -f*_{-d} + G^b / 2 on the F-components
+            for (int m = 0; m < 4; ++m)
+                gb[e][m] = T(2) * (ld_r(fin[idx(d, 2 + m, gx, gy)]) + ld_r(fin[idx(md, 2 + m, x, y)]));
+    }
+    T mu = T(0);
+    double gm0 = 0.0;
+    if (traction) {
+        for (int q = 0; q < 4; ++q)
+            for (int m = 0; m < 4; ++m) cur[q][m] = ld_r(aout[idx(q, 2 + m, x, y)]);
+        mu = a.mufield[(long long)y * a.L.upitch + x];
+        gm0 = a.gmu[(long long)y * a.L.upitch + x];
+    }
+
+    // transposed rules
+    T out[4][6];
+    bool isdest[4] = {false, false, false, false};
+    T UG[4] = {T(0), T(0), T(0), T(0)};
+    double gm = 0.0;
+    for (int e = 0; e < 4; ++e) {
+        if (dest[e] < 0) continue;
+        isdest[dest[e]] = true;
+        if (a.kind[e] == BC_PERIODIC) {
+            for (int k = 0; k < 6; ++k) out[dest[e]][k] = src[e][k];
+            continue;
+        }
         const T sv = (a.kind[e] == BC_VELOCITY) ? T(-1) : T(1);  // D on (v1, v2); -sv on F
-        for (int k = 0; k < 6; ++k) aout[idx(md, k, x, y)] = to_store<S>((k < 2 ? sv : -sv) * cot[k]);
+        for (int k = 0; k < 6; ++k) out[dest[e]][k] = (k < 2 ? sv : -sv) * src[e][k];
         if (a.kind[e] != BC_TRACTION) continue;
         // S_F = G^b / 2 with G^b from N_a P_ia(F^b) = T_i (Sec. 3.6.2)
-        traction = true;
-        T fq[4][6], U[6];
-        for (int q = 0; q < 4; ++q)
-            for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(fin[idx(q, k, x, y)]);
-        state_from_fstar(fq[0], fq[1], fq[2], fq[3], a.hdtb1, a.hdtb2, U);
-        const T mu = a.mufield[(long long)y * a.L.upitch + x], lam = a.lam_ratio * mu;
-        const double gfac = a.g[e] * (a.profile[e] ? a.profile[e][s] : 1.0);
-        const T Tb[2] = {(T)(a.value[e][0] * gfac), (T)(a.value[e][1] * gfac)};
-        T Gb[4] = {U[2], U[3], U[4], U[5]};
-        traction_newton<LAW, T>(e, Gb, Tb, lam, mu);  // a failure was latched by the forward step
+        const LawP<T> mp{a.lam_ratio * mu, mu, T(0), T(0)};
         const int an = (e <= EDGE_RIGHT) ? 0 : 1, tc = 1 - an;
         const T Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? T(-1) : T(1);
         T Jn[2][2], Jt[2][2];
         for (int j = 0; j < 2; ++j) {
             T dF[4] = {T(0), T(0), T(0), T(0)}, dP[4];
             dF[j * 2 + an] = T(1);
-            jvp_ofs<LAW, T>(Gb, dF, lam, mu, dP);
+            jvp_ofs<LAW, T>(gb[e], dF, mp, dP);
             Jn[0][j] = Na * dP[0 * 2 + an];
             Jn[1][j] = Na * dP[1 * 2 + an];
             dF[j * 2 + an] = T(0);
             dF[j * 2 + tc] = T(1);
-            jvp_ofs<LAW, T>(Gb, dF, lam, mu, dP);
+            jvp_ofs<LAW, T>(gb[e], dF, mp, dP);
             Jt[0][j] = Na * dP[0 * 2 + an];
             Jt[1][j] = Na * dP[1 * 2 + an];
         }
-        const T Gbb[4] = {T(0.5) * cot[2], T(0.5) * cot[3], T(0.5) * cot[4], T(0.5) * cot[5]};
+        const T Gbb[4] = {T(0.5) * src[e][2], T(0.5) * src[e][3], T(0.5) * src[e][4], T(0.5) * src[e][5]};
         // z = -Jn^{-T} Gbb_normal
         const T det = Jn[0][0] * Jn[1][1] - Jn[0][1] * Jn[1][0];
         const T r0 = -Gbb[0 * 2 + an], r1 = -Gbb[1 * 2 + an];
@@ -306,18 +338,21 @@ __global__ void __launch_bounds__(128) k_adj_fold(const FoldArgs<typename Prec<S
         const T z1 = (-Jn[0][1] * r0 + Jn[0][0] * r1) / det;
         for (int j = 0; j < 2; ++j) UG[j * 2 + tc] += Gbb[j * 2 + tc] + z0 * Jt[0][j] + z1 * Jt[1][j];
         T Pm[4], dJ;
-        piola_ofs<LAW, T>(Gb[0], Gb[1], Gb[2], Gb[3], a.lam_ratio, T(1), Pm[0], Pm[1], Pm[2], Pm[3], dJ);
+        piola_ofs<LAW, T>(gb[e][0], gb[e][1], gb[e][2], gb[e][3], LawP<T>{a.lam_ratio, T(1), T(0), T(0)}, Pm[0],
+                          Pm[1], Pm[2], Pm[3], dJ);
         gm += (double)(z0 * Na * Pm[0 * 2 + an]) + (double)(z1 * Na * Pm[1 * 2 + an]);
     }
-    if (traction) {
-        // U^n(x_b) = sum_q f*^n_q - (dt/2) B: its cotangent reaches every q
-        for (int q = 0; q < 4; ++q)
-            for (int m = 0; m < 4; ++m) {
-                const long long i = idx(q, 2 + m, x, y);
-                aout[i] = to_store<S>(ld_r(aout[i]) + UG[m]);
-            }
-        a.gmu[(long long)y * a.L.upitch + x] += gm;
+
+    // stores; U^n(x_b) = sum_q f*^n_q - (dt/2) B, so the traction cotangent
+    // of U reaches every q of the node
+    for (int q = 0; q < 4; ++q) {
+        if (isdest[q]) {
+            for (int k = 0; k < 6; ++k) aout[idx(q, k, x, y)] = to_store<S>(out[q][k] + (k >= 2 ? UG[k - 2] : T(0)));
+        } else if (traction) {
+            for (int m = 0; m < 4; ++m) aout[idx(q, 2 + m, x, y)] = to_store<S>(cur[q][m] + UG[m]);
+        }
     }
+    if (traction) a.gmu[(long long)y * a.L.upitch + x] = gm0 + gm;
 }
 
 // ---------------------------------------------------------------- sensors
@@ -380,9 +415,9 @@ __global__ void __launch_bounds__(128) k_adj_init(const AdjInitArgs a)
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
-        double lam, mu, f0[4][6];
-        mat_at(ia.m, n, lam, mu);
-        init_node(ia, x, y, lam, mu, f0);
+        double f0[4][6];
+        const LawP<double> mp = law_at(ia.m, n);
+        init_node(ia, x, y, mp, f0);
         double Un[6];
         for (int k = 0; k < 6; ++k) Un[k] = f0[0][k] + f0[1][k] + f0[2][k] + f0[3][k];
         Un[0] += 0.5 * dt * ia.b1;
@@ -401,8 +436,9 @@ __global__ void __launch_bounds__(128) k_adj_init(const AdjInitArgs a)
         const double ub[2] = {(double)ubar[ui], (double)ubar[ia.L.uplane + ui]};
         const double M[4] = {bX[0], bY[0], bX[1], bY[1]};
         double CM[4], Pm[4], dJ;
-        tangent_jvp(ia.m.law, Fn, M, lam, mu, CM);
-        piola_any(ia.m.law, Gn, ia.m.mufield ? ia.m.lam_ratio : 0.0, 1.0, Pm, dJ);
+        const LawP<double> unit{ia.m.lam_ratio, 1.0, 0.0, 0.0};  // d(lambda, mu)/dmu
+        tangent_jvp(ia.m.law, Fn, M, mp, CM);
+        piola_any(ia.m.law, Gn, unit, Pm, dJ);
         double g[6];
         g[0] = 0.25 * w * Sa[0] - wi2c * (bX[2] + bY[3]) + dt * ub[0];
         g[1] = 0.25 * w * Sa[1] - wi2c * (bX[4] + bY[5]) + dt * ub[1];
@@ -413,8 +449,8 @@ __global__ void __launch_bounds__(128) k_adj_init(const AdjInitArgs a)
         double gm = -wi2c * (M[0] * Pm[0] + M[1] * Pm[1] + M[2] * Pm[2] + M[3] * Pm[3]);
         {
             double fR[4][6], fZ[4][6];
-            init_node(ia, x, y, ia.m.lam_ratio, 1.0, fR);
-            init_node(ia, x, y, 0.0, 0.0, fZ);
+            init_node(ia, x, y, unit, fR);
+            init_node(ia, x, y, LawP<double>{0.0, 0.0, 0.0, 0.0}, fZ);
             for (int q = 0; q < 4; ++q)
                 for (int k = 0; k < 6; ++k) gm += h[q][k] * (fR[q][k] - fZ[q][k]);
         }
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(128) k_adj_init(const AdjInitArgs a)
                 dPb[1] = -0.25 * (2.0 / c) * j * Db[0];
                 dPb[2] = -0.25 * (2.0 / c) * i * Db[1];
                 dPb[3] = -0.25 * (2.0 / c) * j * Db[1];
-                tangent_jvp(ia.m.law, F0, dPb, lam, mu, CdP);  // C^T = C
+                tangent_jvp(ia.m.law, F0, dPb, mp, CdP);  // C^T = C
                 for (int m = 0; m < 4; ++m) Zb[2 + m] += CdP[m];
                 gh[0] += c * i * Zb[0] + Zb[2];
                 gh[1] += c * i * Zb[1] + Zb[4];

@@ -114,6 +114,8 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.src2 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[1]);
     a.lam = (T)c->m.lam;
     a.mu = (T)c->m.mu;
+    a.p2 = (T)c->m.p2;
+    a.p3 = (T)c->m.p3;
     a.mufield = static_cast<const T *>(c->d_muplane);
     a.lam_ratio = (T)c->m.lam_ratio;
     a.c = (T)c->cfg.c;
@@ -301,6 +303,46 @@ lbm_status refresh_ghosts(lbm_ctx *c)
 
 } // namespace
 
+// Parameters of Appendix A per law (SVK, NH, log-NH: lambda, mu; MR: lambda,
+// c10, c01; Yeoh: lambda, c1, c2, c3; Gent: lambda, mu, Jm), copied to p[4];
+// nullptr if valid, else the reason.
+static const char *check_law_params(int law, const double *params, int nparams, double p[4])
+{
+    static const int need[6] = {2, 2, 2, 3, 4, 3};
+    if (law < LBM_LAW_SVK || law > LBM_LAW_GENT) return "unknown law";
+    if (!params || nparams < need[law])
+        return law <= LBM_LAW_LOGNH ? "expected params {lambda, mu}"
+               : law == LBM_LAW_MR  ? "expected params {lambda, c10, c01}"
+               : law == LBM_LAW_YEOH ? "expected params {lambda, c1, c2, c3}"
+                                     : "expected params {lambda, mu, Jm}";
+    for (int i = 0; i < need[law]; ++i) {
+        if (!is_finite(params[i])) return "parameters must be finite";
+        p[i] = params[i];
+    }
+    double mus;  // small-strain shear modulus
+    switch (law) {
+    case LBM_LAW_MR:
+        if (p[1] < 0.0 || p[2] < 0.0) return "c10 and c01 must be >= 0";
+        mus = 2.0 * (p[1] + p[2]);
+        break;
+    case LBM_LAW_YEOH: mus = 2.0 * p[1]; break;
+    case LBM_LAW_GENT:
+        if (!(p[2] > 0.0)) return "Jm must be > 0";
+        mus = p[1];
+        break;
+    default: mus = p[1]; break;
+    }
+    if (!(mus > 0.0)) return "the shear modulus must be > 0";
+    if (!(p[0] + 2.0 * mus > 0.0)) return "lambda + 2 mu must be > 0";
+    return nullptr;
+}
+
+// small-strain shear modulus of the context's material (for the lattice-speed check)
+static double shear_modulus(const Material &m)
+{
+    return m.law == LBM_LAW_MR ? 2.0 * (m.mu + m.p2) : m.law == LBM_LAW_YEOH ? 2.0 * m.mu : m.mu;
+}
+
 static void drop_material_field(lbm_ctx *c)
 {
     cudaFree(c->d_mufield);
@@ -449,18 +491,16 @@ const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_cre
 lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32_t nparams)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
-    if (law == LBM_LAW_MR || law == LBM_LAW_YEOH || law == LBM_LAW_GENT)
-        return fail(c, LBM_ERR_UNSUPPORTED, "Mooney-Rivlin, Yeoh and Gent closures are not built in this version");
-    if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH) return fail(c, LBM_ERR_ARG, "unknown law");
-    if (!params || nparams < 2) return fail(c, LBM_ERR_ARG, "expected params {lambda, mu}");
-    if (!is_finite(params[0]) || !is_finite(params[1]) || !(params[1] > 0.0))
-        return fail(c, LBM_ERR_ARG, "lambda must be finite and mu finite and > 0");
-    if (!(params[0] + 2.0 * params[1] > 0.0)) return fail(c, LBM_ERR_ARG, "lambda + 2 mu must be > 0");
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    const char *msg = check_law_params(law, params, nparams, p);
+    if (msg) return fail(c, LBM_ERR_ARG, msg);
     CK(c, cudaSetDevice(c->cfg.device));
     CK(c, cudaStreamSynchronize(c->st));  // queued steps may still read the old field
-    c->m.law = law; // LBM_LAW_* and tlv::LAW_* share values for SVK, NH, LOGNH
-    c->m.lam = params[0];
-    c->m.mu = params[1];
+    c->m.law = law; // LBM_LAW_* and tlv::LAW_* share values
+    c->m.lam = p[0];
+    c->m.mu = p[1];
+    c->m.p2 = p[2];
+    c->m.p3 = p[3];
     c->have_material = true;
     c->ghosts_dirty = true;  // traction ghosts depend on the material
     drop_material_field(c);
@@ -493,6 +533,7 @@ lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, dou
     CK(c, launch_mu_plane(c->cfg.storage, c->d_mufield, c->d_muplane, c->L, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     c->m.law = law;
+    c->m.p2 = c->m.p3 = 0.0;
     c->m.mufield = c->d_mufield;
     c->m.lam_ratio = lam_ratio;
     // the uniform pair holds the stiffest node, for the lattice-speed check
@@ -588,7 +629,7 @@ static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
     if (order != 0 && order != 2) return fail(c, LBM_ERR_ARG, "order must be 0 or 2");
     lbm_status s = check_edges(c);
     if (s != LBM_OK) return s;
-    const double cP = std::sqrt(c->m.lam + 2.0 * c->m.mu);
+    const double cP = std::sqrt(c->m.lam + 2.0 * shear_modulus(c->m));
     if (!(c->cfg.c > cP)) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "lattice speed c = %g must exceed the P-wave speed sqrt(lambda + 2 mu) = %g",

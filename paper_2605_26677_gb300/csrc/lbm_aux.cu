@@ -18,9 +18,9 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
-        double lam, mu, f[4][6];
-        mat_at(a.m, n, lam, mu);
-        if (!init_node(a, x, y, lam, mu, f)) atomicOr(a.status, ST_BAD_J);
+        double f[4][6];
+        const LawP<double> m = law_at(a.m, n);
+        if (!init_node(a, x, y, m, f)) atomicOr(a.status, ST_BAD_J);
         // step-0 collision (Eqs. 10, 12, 14)
         double Un[6], dJ;
         for (int k = 0; k < 6; ++k) Un[k] = f[0][k] + f[1][k] + f[2][k] + f[3][k];
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
         Un[1] += 0.5 * dt * a.b2;
         const double Gn[4] = {Un[2] - 1.0, Un[3], Un[4], Un[5] - 1.0};
         double Pn[4], feq[4][6];
-        piola_any(a.m.law, Gn, lam, mu, Pn, dJ);
+        piola_any(a.m.law, Gn, m, Pn, dJ);
         feq_full(Un, Pn, c, feq);
         const double src[2] = {dt * (2.0 - a.omega) * 0.125 * a.b1, dt * (2.0 - a.omega) * 0.125 * a.b2};
         for (int q = 0; q < 4; ++q)
@@ -83,9 +83,8 @@ __global__ void __launch_bounds__(128) k_read(const ReadArgs a)
             a.U[5 * N + n] = 1.0 + G[3];
         }
         if (a.P || a.sigma) {
-            double P[4], dJ, lam, mu;
-            mat_at(a.m, n, lam, mu);
-            piola_any(a.m.law, G, lam, mu, P, dJ);
+            double P[4], dJ;
+            piola_any(a.m.law, G, law_at(a.m, n), P, dJ);
             if (a.P)
                 for (int m = 0; m < 4; ++m) a.P[m * N + n] = P[m];
             if (a.sigma) {
@@ -182,9 +181,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const DiagArgs a)
         r.s[0] += v1;
         r.s[1] += v2;
         for (int m = 0; m < 4; ++m) r.s[2 + m] += S[2 + m];
-        double lam, mu;
-        mat_at(a.m, n, lam, mu);
-        r.s[6] += 0.5 * (v1 * v1 + v2 * v2) + energy_ofs(a.m.law, S[2], S[3], S[4], S[5], lam, mu);
+        r.s[6] += 0.5 * (v1 * v1 + v2 * v2) + energy_ofs(a.m.law, S[2], S[3], S[4], S[5], law_at(a.m, n));
         r.jmin = fmin(r.jmin, 1.0 + dJ);
         r.jmax = fmax(r.jmax, 1.0 + dJ);
         r.gmax = fmax(r.gmax, sqrt(S[2] * S[2] + S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));

@@ -100,6 +100,9 @@ const void *batch_kernel(int law, int vec)
     case LAW_SVK: return batch_kernel_law<S, LAW_SVK>(vec);
     case LAW_NH: return batch_kernel_law<S, LAW_NH>(vec);
     case LAW_LOGNH: return batch_kernel_law<S, LAW_LOGNH>(vec);
+    case LAW_MR: return batch_kernel_law<S, LAW_MR>(vec);
+    case LAW_YEOH: return batch_kernel_law<S, LAW_YEOH>(vec);
+    case LAW_GENT: return batch_kernel_law<S, LAW_GENT>(vec);
     default: return nullptr;
     }
 }

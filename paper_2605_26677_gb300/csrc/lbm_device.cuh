@@ -77,7 +77,7 @@ __host__ auto with_storage(int storage, Fn fn)
 
 enum { EDGE_LEFT = 0, EDGE_RIGHT = 1, EDGE_BOTTOM = 2, EDGE_TOP = 3 };
 enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_TRACTION = 2 };
-enum { LAW_SVK = 0, LAW_NH = 1, LAW_LOGNH = 2 };
+enum { LAW_SVK = 0, LAW_NH = 1, LAW_LOGNH = 2, LAW_MR = 3, LAW_YEOH = 4, LAW_GENT = 5 };
 enum { TF_CONST = 0, TF_LINEAR_RAMP = 1, TF_SIN2_RAMP = 2, TF_SIN_PULSE = 3, TF_RICKER = 4 };
 enum { FB_NODE = 0, FB_EXTRAP2 = 1 };
 enum { ST_BAD_J = 1, ST_NEWTON = 2, ST_NONFINITE = 4 };
@@ -91,23 +91,42 @@ struct Layout {
     int upitch;       // doubles per u* row (no ghost rows or columns)
 };
 
+// Closure parameters as the law lists them (Appendix A): lam = lambda and
+// mu, p2, p3 the law's own (SVK, NH, log-NH: mu; MR: c10, c01; Yeoh: c1,
+// c2, c3; Gent: mu, Jm).
+template <typename R>
+struct LawP {
+    R lam, mu, p2, p3;
+};
+
 struct Material {
     int law;
-    double lam, mu;
-    const double *mufield;  // per-node mu (compact, node y * nx + x) or nullptr
+    double lam, mu, p2, p3;
+    const double *mufield;  // per-node mu (compact, node y * nx + x) or nullptr (SVK, NH, log-NH)
     double lam_ratio;       // lambda = lam_ratio * mu where mufield is set
 };
 
-// (lambda, mu) of node n (compact index)
-__device__ __forceinline__ void mat_at(const Material &m, long long n, double &lam, double &mu)
+// parameters of node n (compact index)
+__host__ __device__ __forceinline__ LawP<double> law_at(const Material &m, long long n)
 {
     if (m.mufield) {
-        mu = m.mufield[n];
-        lam = m.lam_ratio * mu;
-    } else {
-        lam = m.lam;
-        mu = m.mu;
+        const double mu = m.mufield[n];
+        return LawP<double>{m.lam_ratio * mu, mu, 0.0, 0.0};
     }
+    return LawP<double>{m.lam, m.mu, m.p2, m.p3};
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ LawP<R> law_cast(const LawP<double> &m)
+{
+    return LawP<R>{(R)m.lam, (R)m.mu, (R)m.p2, (R)m.p3};
+}
+
+// small-strain shear modulus of the law (a stress scale for tolerances)
+template <int LAW, typename R>
+__host__ __device__ __forceinline__ R shear_scale(const LawP<R> &m)
+{
+    return LAW == LAW_MR ? R(2) * (m.mu + m.p2) : LAW == LAW_YEOH ? R(2) * m.mu : m.mu;
 }
 
 struct EdgeDesc {
@@ -129,6 +148,7 @@ struct StepArgs {
     T hdtb1, hdtb2;              // (dt/2) b
     T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
     T lam, mu, c;
+    T p2, p3;                    // third and fourth closure parameters (MR, Yeoh, Gent)
     const T *mufield;            // per-node mu in the u* plane layout, read by the MATF kernels
     T lam_ratio;                 // lambda = lam_ratio * mu there
     double dt;
@@ -173,13 +193,103 @@ struct EdgeArgs {
 };
 
 // ---------------------------------------------------------------- pointwise
+using ::expm1;  // the overloads below add Dual versions to these
+using ::log1p;
+
+// Forward-mode dual numbers v + d eps (eps^2 = 0): the Jacobian action of a
+// closure written once for the value type is its evaluation on duals.
+template <typename R>
+struct Dual {
+    R v, d;
+    __host__ __device__ Dual() {}
+    __host__ __device__ Dual(R x) : v(x), d(R(0)) {}
+    __host__ __device__ Dual(R x, R y) : v(x), d(y) {}
+};
+template <typename R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a) { return {-a.v, -a.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, Dual<R> b)
+{
+    const R q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+template <typename R> __device__ __forceinline__ Dual<R> operator*(R a, Dual<R> b) { return {a * b.v, a * b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator+(R a, Dual<R> b) { return {a + b.v, b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator-(R a, Dual<R> b) { return {a - b.v, -b.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, R b) { return {a.v * b, a.d * b}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, R b) { return {a.v + b, a.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, R b) { return {a.v - b, a.d}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, R b) { return {a.v / b, a.d / b}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator/(R a, Dual<R> b)
+{
+    const R q = a / b.v;
+    return {q, -q * b.d / b.v};
+}
+template <typename R> __device__ __forceinline__ Dual<R> log1p(Dual<R> a) { return {::log1p(a.v), a.d / (R(1) + a.v)}; }
+template <typename R> __device__ __forceinline__ Dual<R> expm1(Dual<R> a)
+{
+    const R e = ::expm1(a.v);
+    return {e, (R(1) + e) * a.d};
+}
+
+// Closures built on the isochoric invariants (Eqs. A.2-A.3, A.7-A.9), from
+// G = F - I in a form without cancellation at F = I: with tc = tr C - 2,
+// J - 1 = dJ, J^{-2/3} = 1 + j23 and J^{-4/3} = 1 + j43 (expm1 of the scaled
+// log1p), I1 = 3 + tc, I2 = 3 + dJ (2 + dJ) + tc (C33 = 1):
+//   dI1bar/dF = (1 + j23) [2 (F - H) - (2/3) tc H]
+//   dI2bar/dF = (1 + j43) [2 (F - H) + ((2/3) dJ (2 + dJ) - (4/3) tc) H]
+//   P = s1 dI1bar/dF + s2 dI2bar/dF + lambda log J H,
+// s1 = c10, s2 = c01 (MR); s1 = c1 + 2 c2 A + 3 c3 A^2 (Yeoh); s1 = mu / (2 (1 - A / Jm))
+// (Gent), A = I1bar - 3 = 3 j23 + tc + j23 tc. V is R or Dual<R>.
+template <int LAW, typename V, typename R>
+__device__ __forceinline__ void piola_inv(const V G[4], const LawP<R> &m, V P[4], V &dJ)
+{
+    dJ = G[0] + G[3] + (G[0] * G[3] - G[1] * G[2]);
+    const V J = R(1) + dJ;
+    const V invJ = V(R(1)) / J;
+    const V FmH[4] = {(G[0] - G[3] + dJ * (R(1) + G[0])) * invJ, (G[1] * J + G[2]) * invJ,
+                      (G[2] * J + G[1]) * invJ, (G[3] - G[0] + dJ * (R(1) + G[3])) * invJ};
+    const V H[4] = {(R(1) + G[3]) * invJ, -(G[2] * invJ), -(G[1] * invJ), (R(1) + G[0]) * invJ};
+    const V tc = R(2) * (G[0] + G[3]) + (G[0] * G[0] + G[1] * G[1]) + (G[2] * G[2] + G[3] * G[3]);
+    const V lJ = log1p(dJ);
+    const V j23 = expm1(R(-2.0 / 3.0) * lJ);
+    const V A = R(3) * j23 + tc + j23 * tc;
+    V s1;
+    if (LAW == LAW_MR)
+        s1 = V(m.mu);
+    else if (LAW == LAW_YEOH)
+        s1 = m.mu + (R(2) * m.p2) * A + (R(3) * m.p3) * (A * A);
+    else
+        s1 = m.mu / (R(2) * (R(1) - A / V(m.p2)));
+    const V c1 = R(2.0 / 3.0) * tc;
+    const V vol = m.lam * lJ;
+    for (int k = 0; k < 4; ++k) P[k] = s1 * ((R(1) + j23) * (R(2) * FmH[k] - c1 * H[k])) + vol * H[k];
+    if (LAW == LAW_MR) {
+        const V j43 = expm1(R(-4.0 / 3.0) * lJ);
+        const V c2 = R(2.0 / 3.0) * (dJ * (R(2) + dJ)) - R(4.0 / 3.0) * tc;
+        for (int k = 0; k < 4; ++k) P[k] = P[k] + m.p2 * ((R(1) + j43) * (R(2) * FmH[k] + c2 * H[k]));
+    }
+}
+
 // First Piola stress from G = F - I (Appendix A), written so that the rest
 // state does not cancel catastrophically: J - 1 = G11 + G22 + G11 G22 - G12 G21.
 // Returns J - 1 in dJ.
 template <int LAW, typename R>
-__device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, R lam, R mu, R &P11, R &P12,
+__device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, const LawP<R> &m, R &P11, R &P12,
                                           R &P21, R &P22, R &dJ)
 {
+    const R lam = m.lam, mu = m.mu;
+    if (LAW >= LAW_MR) {
+        const R G[4] = {G11, G12, G21, G22};
+        R P[4];
+        piola_inv<LAW, R, R>(G, m, P, dJ);
+        P11 = P[0];
+        P12 = P[1];
+        P21 = P[2];
+        P22 = P[3];
+        return;
+    }
     dJ = G11 + G22 + (G11 * G22 - G12 * G21);
     if (LAW == LAW_SVK) {
         // Eq. (A.4): P = F S, S = lambda tr(E) I + 2 mu E, E = (G + G^T + G^T G) / 2
@@ -209,10 +319,34 @@ __device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, R lam, R m
     }
 }
 
+// dP = C : dF for the invariant-based closures, by dual numbers
+template <int LAW, typename R>
+__device__ __forceinline__ void jvp_inv(const R G[4], const R dF[4], const LawP<R> &m, R dP[4])
+{
+    Dual<R> Gd[4], Pd[4], dJ;
+    for (int k = 0; k < 4; ++k) Gd[k] = Dual<R>(G[k], dF[k]);
+    piola_inv<LAW, Dual<R>, R>(Gd, m, Pd, dJ);
+    for (int k = 0; k < 4; ++k) dP[k] = Pd[k].d;
+}
+
+// FP64 stress of any law chosen at run time, from G = F - I
+__device__ inline void piola_any(int law, const double G[4], const LawP<double> &m, double P[4], double &dJ)
+{
+    switch (law) {
+    case LAW_SVK: piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_NH: piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_LOGNH: piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_MR: piola_ofs<LAW_MR, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_YEOH: piola_ofs<LAW_YEOH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    default: piola_ofs<LAW_GENT, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    }
+}
+
 // Strain energy W(F) of the same laws (diagnostics only), from G = F - I.
 __device__ __forceinline__ double energy_ofs(int law, double G11, double G12, double G21, double G22,
-                                             double lam, double mu)
+                                             const LawP<double> &m)
 {
+    const double lam = m.lam, mu = m.mu;
     const double dJ = G11 + G22 + (G11 * G22 - G12 * G21);
     if (law == LAW_SVK) {
         const double E11 = G11 + 0.5 * (G11 * G11 + G21 * G21);
@@ -225,13 +359,35 @@ __device__ __forceinline__ double energy_ofs(int law, double G11, double G12, do
     const double trCm2 = 2.0 * (G11 + G22) + G11 * G11 + G12 * G12 + G21 * G21 + G22 * G22;
     const double lJ = log1p(dJ);
     if (law == LAW_NH) return 0.5 * mu * (trCm2 - 2.0 * lJ) + 0.25 * lam * (dJ * (2.0 + dJ) - 2.0 * lJ);
-    return 0.5 * mu * (trCm2 - 2.0 * lJ) + 0.5 * lam * lJ * lJ;
+    if (law == LAW_LOGNH) return 0.5 * mu * (trCm2 - 2.0 * lJ) + 0.5 * lam * lJ * lJ;
+    // Eqs. (A.7)-(A.9) with the variables of piola_inv
+    const double j23 = expm1(-2.0 / 3.0 * lJ);
+    const double A = 3.0 * j23 + trCm2 + j23 * trCm2;
+    const double vol = 0.5 * lam * lJ * lJ;
+    if (law == LAW_MR) {
+        const double j43 = expm1(-4.0 / 3.0 * lJ);
+        const double s = dJ * (2.0 + dJ) + trCm2;
+        return mu * A + m.p2 * (3.0 * j43 + s + j43 * s) + vol;
+    }
+    if (law == LAW_YEOH) return mu * A + m.p2 * A * A + m.p3 * A * A * A + vol;
+    return -0.5 * mu * m.p2 * log1p(-A / m.p2) + vol;
 }
 
 // Jacobian-vector product dP = C : dF of the tangent of Eq. (4) (Eq. 8), FP64.
-__device__ __forceinline__ void tangent_jvp(int law, const double F[4], const double dF[4], double lam,
-                                            double mu, double dP[4])
+__device__ __forceinline__ void tangent_jvp(int law, const double F[4], const double dF[4], const LawP<double> &m,
+                                            double dP[4])
 {
+    const double lam = m.lam, mu = m.mu;
+    if (law >= LAW_MR) {
+        const double G[4] = {F[0] - 1.0, F[1], F[2], F[3] - 1.0};
+        if (law == LAW_MR)
+            jvp_inv<LAW_MR, double>(G, dF, m, dP);
+        else if (law == LAW_YEOH)
+            jvp_inv<LAW_YEOH, double>(G, dF, m, dP);
+        else
+            jvp_inv<LAW_GENT, double>(G, dF, m, dP);
+        return;
+    }
     if (law == LAW_SVK) {
         // dP = dF S + F dS, dS = lambda tr(dE) I + 2 mu dE, dE = (dF^T F + F^T dF) / 2
         const double E11 = 0.5 * (F[0] * F[0] + F[2] * F[2] - 1.0);

@@ -34,8 +34,13 @@ __device__ __forceinline__ float newton_tol<float>(float tmax, float mu, float g
 
 // dP = C : dF (Eq. 8) in precision R, from G = F - I
 template <int LAW, typename R>
-__device__ __forceinline__ void jvp_ofs(const R G[4], const R dF[4], R lam, R mu, R dP[4])
+__device__ __forceinline__ void jvp_ofs(const R G[4], const R dF[4], const LawP<R> &m, R dP[4])
 {
+    if (LAW >= LAW_MR) {
+        jvp_inv<LAW, R>(G, dF, m, dP);
+        return;
+    }
+    const R lam = m.lam, mu = m.mu;
     const R F[4] = {R(1) + G[0], G[1], G[2], R(1) + G[3]};
     if (LAW == LAW_SVK) {
         const R E11 = G[0] + R(0.5) * (G[0] * G[0] + G[2] * G[2]);
@@ -87,24 +92,25 @@ __device__ __forceinline__ void jvp_ofs(const R G[4], const R dF[4], R lam, R mu
 // only decreasing |r|). G holds F - I at the node; the result replaces it.
 // Returns false if the tolerance was not reached.
 template <int LAW, typename R>
-__device__ bool traction_newton(int e, R G[4], const R Tb[2], R lam, R mu)
+__device__ bool traction_newton(int e, R G[4], const R Tb[2], const LawP<R> &m)
 {
+    const R mus = shear_scale<LAW, R>(m);
     const int an = (e <= EDGE_RIGHT) ? 0 : 1;
     const R Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? R(-1) : R(1);
     R P[4], dJ, r[2];
-    piola_ofs<LAW, R>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
+    piola_ofs<LAW, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ);
     r[0] = Na * P[0 * 2 + an] - Tb[0];
     r[1] = Na * P[1 * 2 + an] - Tb[1];
     const R tmax = fmax(fabs(Tb[0]), fabs(Tb[1]));
     for (int it = 0; it < 20; ++it) {
         const R gmax = fmax(fmax(fabs(G[0]), fabs(G[1])), fmax(fabs(G[2]), fabs(G[3])));
-        if (fmax(fabs(r[0]), fabs(r[1])) <= newton_tol<R>(tmax, mu, gmax)) return true;
+        if (fmax(fabs(r[0]), fabs(r[1])) <= newton_tol<R>(tmax, mus, gmax)) return true;
         R Jac[2][2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             R dF[4] = {R(0), R(0), R(0), R(0)}, dP[4];
             dF[k * 2 + an] = R(1);
-            jvp_ofs<LAW, R>(G, dF, lam, mu, dP);
+            jvp_ofs<LAW, R>(G, dF, m, dP);
             Jac[0][k] = Na * dP[0 * 2 + an];
             Jac[1][k] = Na * dP[1 * 2 + an];
         }
@@ -121,7 +127,7 @@ __device__ bool traction_newton(int e, R G[4], const R Tb[2], R lam, R mu)
             Gt[0 * 2 + an] += alpha * d0;
             Gt[1 * 2 + an] += alpha * d1;
             R Pt[4], dJt;
-            piola_ofs<LAW, R>(Gt[0], Gt[1], Gt[2], Gt[3], lam, mu, Pt[0], Pt[1], Pt[2], Pt[3], dJt);
+            piola_ofs<LAW, R>(Gt[0], Gt[1], Gt[2], Gt[3], m, Pt[0], Pt[1], Pt[2], Pt[3], dJt);
             if (dJt > R(-1)) {
                 const R rt0 = Na * Pt[0 * 2 + an] - Tb[0], rt1 = Na * Pt[1 * 2 + an] - Tb[1];
                 if (hypot(rt0, rt1) < rn) {
@@ -138,7 +144,7 @@ __device__ bool traction_newton(int e, R G[4], const R Tb[2], R lam, R mu)
         if (!accepted) break;
     }
     const R gmax = fmax(fmax(fabs(G[0]), fabs(G[1])), fmax(fabs(G[2]), fabs(G[3])));
-    return fmax(fabs(r[0]), fabs(r[1])) <= newton_tol<R>(tmax, mu, gmax);
+    return fmax(fabs(r[0]), fabs(r[1])) <= newton_tol<R>(tmax, mus, gmax);
 }
 
 // Ghost value of a velocity or traction edge in the node form. fo: f*_{-d}
@@ -146,7 +152,7 @@ __device__ bool traction_newton(int e, R G[4], const R Tb[2], R lam, R mu)
 // at t^n + dt/2. Writes out[6]; sets ST_NEWTON in flags on failure.
 template <int LAW, typename R>
 __device__ __forceinline__ void edge_ghost(int e, int kind, const R fo[6], const R U[6], const double val[2],
-                                           R c, R lam, R mu, R out[6], unsigned &flags)
+                                           R c, const LawP<R> &m, R out[6], unsigned &flags)
 {
     const R N0 = (e == EDGE_LEFT) ? R(-1) : (e == EDGE_RIGHT) ? R(1) : R(0);
     const R N1 = (e == EDGE_BOTTOM) ? R(-1) : (e == EDGE_TOP) ? R(1) : R(0);
@@ -163,7 +169,7 @@ __device__ __forceinline__ void edge_ghost(int e, int kind, const R fo[6], const
         // Eq. (25): D = diag(1,1,-1,-1,-1,-1), S = (T/c, F^b/2)
         R G[4] = {U[2], U[3], U[4], U[5]};
         const R Tb[2] = {v0, v1};
-        if (!traction_newton<LAW, R>(e, G, Tb, lam, mu)) flags |= ST_NEWTON;
+        if (!traction_newton<LAW, R>(e, G, Tb, m)) flags |= ST_NEWTON;
         out[0] = fo[0] + v0 / c;
         out[1] = fo[1] + v1 / c;
 #pragma unroll

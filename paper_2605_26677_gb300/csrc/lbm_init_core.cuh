@@ -12,15 +12,6 @@ __device__ __forceinline__ long long pidx(const Layout &L, int q, int k, int x, 
     return (long long)(q * 6 + k) * L.plane + (long long)(y + 1) * L.pitch + L.xoff + x;
 }
 
-__device__ inline void piola_any(int law, const double G[4], double lam, double mu, double P[4], double &dJ)
-{
-    if (law == LAW_SVK)
-        piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else if (law == LAW_NH)
-        piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else
-        piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-}
 
 // Second-order difference of a compact field along x (dir 0) or y (dir 1):
 // central inside, wrap-around when periodic, one-sided three-point stencil at
@@ -48,8 +39,8 @@ __device__ __forceinline__ void feq_full(const double U[6], const double P[4], d
 
 // f^0 at node (x, y) in full (not offset) form: f^eq(U0) and, for order 2,
 // the correction -(dt/2) D_q f^eq of Eqs. (16)-(21), with the node's
-// (lambda, mu). Returns false if det F0 <= 0.
-__device__ inline bool init_node(const InitArgs &a, int x, int y, double lam, double mu, double f[4][6])
+// parameters. Returns false if det F0 <= 0.
+__device__ inline bool init_node(const InitArgs &a, int x, int y, const LawP<double> &m, double f[4][6])
 {
     const int nx = a.L.nx, ny = a.L.ny;
     const long long N = (long long)nx * ny, n = (long long)y * nx + x;
@@ -60,7 +51,7 @@ __device__ inline bool init_node(const InitArgs &a, int x, int y, double lam, do
     const double F[4] = {U[2], U[3], U[4], U[5]};
     const double G[4] = {U[2] - 1.0, U[3], U[4], U[5] - 1.0};
     double P[4], dJ;
-    piola_any(a.m.law, G, lam, mu, P, dJ);
+    piola_any(a.m.law, G, m, P, dJ);
     feq_full(U, P, c, f);
     if (a.order == 2) {
         double gX[6], gY[6], dPX[4], dPY[4];
@@ -69,8 +60,8 @@ __device__ inline bool init_node(const InitArgs &a, int x, int y, double lam, do
             gY[k] = fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, a.dx);
         }
         // d_alpha P = C : d_alpha F (text after Eq. 18), as Jacobian actions (Eq. 8)
-        tangent_jvp(a.m.law, F, gX + 2, lam, mu, dPX);
-        tangent_jvp(a.m.law, F, gY + 2, lam, mu, dPY);
+        tangent_jvp(a.m.law, F, gX + 2, m, dPX);
+        tangent_jvp(a.m.law, F, gY + 2, m, dPY);
         for (int q = 0; q < 4; ++q) {
             const double i = ci[q], j = cj[q];
             double Z[6], dP[4];
@@ -81,7 +72,7 @@ __device__ inline bool init_node(const InitArgs &a, int x, int y, double lam, do
             Z[3] = gY[0] + c * i * gX[3] + c * j * gY[3];
             Z[4] = gX[1] + c * i * gX[4] + c * j * gY[4];
             Z[5] = gY[1] + c * i * gX[5] + c * j * gY[5];
-            tangent_jvp(a.m.law, F, Z + 2, lam, mu, dP); // Eq. (20)
+            tangent_jvp(a.m.law, F, Z + 2, m, dP); // Eq. (20)
             // Eq. (21): D_q f^eq = (f^eq)'(U0) Z_q, then Eq. (16)
             const double Dq[6] = {0.25 * (Z[0] - (2.0 / c) * (i * dP[0] + j * dP[1])),
                                   0.25 * (Z[1] - (2.0 / c) * (i * dP[2] + j * dP[3])),

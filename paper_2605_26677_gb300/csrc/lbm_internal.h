@@ -114,9 +114,7 @@ struct FoldArgs {
     double *gmu;
     Layout L;
     int kind[4];
-    double value[4][2], g[4];  // edge data of the ghosts of f*^n: value * g * profile
-    const double *profile[4];
-    T hdtb1, hdtb2, lam_ratio;
+    T lam_ratio;
     int count;                 // boundary ring nodes
 };
 struct RecordArgs {

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_noalloc_partial(const Noall
         acc.s[3] += G12;
         acc.s[4] += G21;
         acc.s[5] += G22;
-        acc.s[6] += 0.5 * (v1 * v1 + v2 * v2) + tlv::energy_ofs(a.m.law, G11, G12, G21, G22, a.m.lam, a.m.mu);
+        acc.s[6] += 0.5 * (v1 * v1 + v2 * v2) + tlv::energy_ofs(a.m.law, G11, G12, G21, G22, tlv::law_at(a.m, 0));
         acc.jmin = fmin(acc.jmin, J);
         acc.jmax = fmax(acc.jmax, J);
         acc.gmax = fmax(acc.gmax, sqrt(G11 * G11 + G12 * G12 + G21 * G21 + G22 * G22));
@@ -184,9 +184,9 @@ extern "C" lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t
     if (N > max_nodes)
         return noalloc_fail(LBM_ERR_ARG, "grid of " + std::to_string(N) + " nodes exceeds the static scratch "
                                          "capacity of " + std::to_string(max_nodes) + " nodes");
-    if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH)
-        return noalloc_fail(LBM_ERR_UNSUPPORTED, "only the SVK, NH and log-NH closures are supported");
-    if (!params || nparams < 2 || !(params[1] > 0.0)) return noalloc_fail(LBM_ERR_ARG, "params must be {lambda, mu > 0}");
+    static const int need[6] = {2, 2, 2, 3, 4, 3};
+    if (law < LBM_LAW_SVK || law > LBM_LAW_GENT) return noalloc_fail(LBM_ERR_ARG, "unknown law");
+    if (!params || nparams < need[law]) return noalloc_fail(LBM_ERR_ARG, "too few closure parameters");
     if (!(dx > 0.0)) return noalloc_fail(LBM_ERR_ARG, "dx must be > 0");
     if (device < 0 || device >= NOALLOC_MAX_DEVICES) return noalloc_fail(LBM_ERR_ARG, "device ordinal out of range");
     cudaError_t e = cudaSetDevice(device);
@@ -209,6 +209,8 @@ extern "C" lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t
     a.m.law = law;
     a.m.lam = params[0];
     a.m.mu = params[1];
+    a.m.p2 = nparams > 2 ? params[2] : 0.0;
+    a.m.p3 = nparams > 3 ? params[3] : 0.0;
     a.m.mufield = nullptr;
     a.m.lam_ratio = 0.0;
     a.dx = dx;

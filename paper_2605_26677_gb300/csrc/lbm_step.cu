@@ -1,4 +1,7 @@
-// lbm_step.cu -- the single-lattice step kernels of the TL vectorial D2Q4x6 LBM.
+// lbm_step.cu -- the edge kernel of the extrapolated F^b form and the
+// dispatch of the single-lattice step kernels of the TL vectorial D2Q4x6 LBM
+// (the kernels themselves: lbm_step_kernels.cuh, one storage type per
+// translation unit).
 //
 // One time step (Sec. 3.7) is one launch of k_step (k_step16 for 16-bit
 // storage): fused pull-streaming (Eq. 15) + state recovery (Eq. 10) + P(F) +
@@ -15,84 +18,6 @@
 #include "lbm_step_core.cuh"
 
 namespace tlv {
-template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
-__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
-{
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
-    unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF>(a, task, lane, flags);
-    flags = __reduce_or_sync(FULL_MASK, flags);
-    if (flags && lane == 0) atomicOr(a.status, (int)flags);
-}
-
-template <typename S, int LAW, int V, bool FUSE>
-__global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
-{
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    const int ntask = a.L.ny * ((a.L.nx + 32 * V - 1) / (32 * V));
-    unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE>(a, task, lane, flags);
-    flags = __reduce_or_sync(FULL_MASK, flags);
-    if (flags && lane == 0) atomicOr(a.status, (int)flags);
-}
-
-// Ghost refresh in the node form (after initialization, a checkpoint load or
-// new edge data): the same values the fused step writes, from the stored
-// post-collision populations of the current buffer.
-template <typename S, int LAW>
-__global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
-{
-    using T = typename Prec<S>::R;
-    S *f = static_cast<S *>(a.f);
-    int e = 0;
-    while (e < 3 && (int)blockIdx.x >= a.blk_end[e]) ++e;
-    const int b0 = e ? a.blk_end[e - 1] : 0;
-    const int s = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x;
-    const int len = (e <= EDGE_RIGHT) ? a.L.ny : a.L.nx;
-    if (s >= len) return;
-    auto idx = [&](int q, int k, int x, int y) {
-        return (long long)(q * 6 + k) * a.L.plane + (long long)(y + 1) * a.L.pitch + a.L.xoff + x;
-    };
-    int xb, yb, gx, gy;
-    switch (e) {
-    case EDGE_LEFT: xb = 0; yb = s; gx = -1; gy = s; break;
-    case EDGE_RIGHT: xb = a.L.nx - 1; yb = s; gx = a.L.nx; gy = s; break;
-    case EDGE_BOTTOM: xb = s; yb = 0; gx = s; gy = -1; break;
-    default: xb = s; yb = a.L.ny - 1; gx = s; gy = a.L.ny; break;
-    }
-    const int d = edge_dmiss(e), md = edge_dout(e);
-    const EdgeDesc &E = a.e[e];
-    if (E.kind == BC_PERIODIC) {
-        const int sx = (e == EDGE_LEFT) ? a.L.nx - 1 : (e == EDGE_RIGHT) ? 0 : s;
-        const int sy = (e == EDGE_BOTTOM) ? a.L.ny - 1 : (e == EDGE_TOP) ? 0 : s;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = f[idx(d, k, sx, sy)];
-        return;
-    }
-    T fq[4][6], U[6], fo[6], out[6];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(f[idx(q, k, xb, yb)]);
-    state_from_fstar(fq[0], fq[1], fq[2], fq[3], (T)a.hdtb1, (T)a.hdtb2, U);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) fo[k] = fq[md][k];
-    double val[2];
-    edge_value(E, s, a.g[e], val);
-    unsigned flags = 0;
-    double lam, mu;
-    mat_at(a.m, (long long)yb * a.L.nx + xb, lam, mu);
-    edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, (T)lam, (T)mu, out, flags);
-    if (flags) atomicOr(a.status, (int)flags);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = to_store<S>(out[k]);
-}
-
 // ---------------------------------------------------------------- edges
 template <typename T>
 struct EdgeView {
@@ -131,15 +56,6 @@ __device__ void node_state(const EdgeView<T> &v, int x, int y, double hb1, doubl
     U[1] -= hb2;
 }
 
-__device__ void piola_law(int law, const double G[4], double lam, double mu, double P[4], double &dJ)
-{
-    if (law == LAW_SVK)
-        piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else if (law == LAW_NH)
-        piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-    else
-        piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], lam, mu, P[0], P[1], P[2], P[3], dJ);
-}
 
 // tangential derivative of v_i along edge e in layer `layer` at position s:
 // central difference, wrap-around when the tangential direction is periodic,
@@ -190,8 +106,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
     const double Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? -1.0 : 1.0;
     int x0, y0;
     edge_node(a.L, e, 0, s, x0, y0);
-    double lam, mu;
-    mat_at(a.m, (long long)y0 * a.L.nx + x0, lam, mu);
+    const LawP<double> m = law_at(a.m, (long long)y0 * a.L.nx + x0);
     double U0[6];
     node_state(v, x0, y0, a.hdtb1, a.hdtb2, U0);
     if (a.fb_mode == FB_EXTRAP2) {
@@ -213,7 +128,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
     const double tmax = fmax(fabs(Tb[0]), fabs(Tb[1]));
     const double tol = 1e-13 * (tmax > 1.0 ? tmax : 1.0);
     double P[4], dJ, r[2];
-    piola_law(a.m.law, Gb, lam, mu, P, dJ);
+    piola_any(a.m.law, Gb, m, P, dJ);
     r[0] = Na * P[0 * 2 + an] - Tb[0];
     r[1] = Na * P[1 * 2 + an] - Tb[1];
     for (int it = 0; it < 20; ++it) {
@@ -223,7 +138,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
         for (int k = 0; k < 2; ++k) {
             double dF[4] = {0.0, 0.0, 0.0, 0.0}, dP[4];
             dF[k * 2 + an] = 1.0;
-            tangent_jvp(a.m.law, F, dF, lam, mu, dP);
+            tangent_jvp(a.m.law, F, dF, m, dP);
             Jac[0][k] = Na * dP[0 * 2 + an];
             Jac[1][k] = Na * dP[1 * 2 + an];
         }
@@ -240,7 +155,7 @@ __device__ bool traction_Fb(const EdgeView<T> &v, const EdgeArgs &a, int e, int 
             const double Jt = (1.0 + Gt[0]) * (1.0 + Gt[3]) - Gt[1] * Gt[2];
             if (Jt > 0.0) {
                 double Pt[4], dJt, rt[2];
-                piola_law(a.m.law, Gt, lam, mu, Pt, dJt);
+                piola_any(a.m.law, Gt, m, Pt, dJt);
                 rt[0] = Na * Pt[0 * 2 + an] - Tb[0];
                 rt[1] = Na * Pt[1 * 2 + an] - Tb[1];
                 if (hypot(rt[0], rt[1]) < rn) {
@@ -315,53 +230,45 @@ __global__ void __launch_bounds__(128) k_edges(const EdgeArgs a)
         v.f[v.idx(d, k, gx, gy)] = to_store<T>(D[k] * (double)ld_r(v.f[v.idx(md, k, xb, yb)]) + S[k]);
 }
 
-// ---------------------------------------------------------------- launchers
-template <typename S, int LAW>
-static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
-{
-    if (a.mufield) {
-        // per-node material: FP64 and FP32 storage
-        if constexpr (sizeof(S) == 2) {
-            return cudaErrorNotSupported;
-        } else {
-            if (fuse)
-                k_step<S, LAW, 16 / sizeof(S), true, true><<<grid, 128, 0, st>>>(a);
-            else
-                k_step<S, LAW, 16 / sizeof(S), false, true><<<grid, 128, 0, st>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    if constexpr (sizeof(S) == 2) {
-        if (fuse)
-            k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);
-        else
-            k_step16<S, LAW, STEP16_V, false><<<grid, 128, 0, st>>>(a);
-    } else {
-        constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors
-        if (fuse)
-            k_step<S, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
-        else
-            k_step<S, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
-    }
-    return cudaGetLastError();
-}
-
-template <typename S>
-static cudaError_t launch_step_law(int law, const void *args, bool fuse, int grid, cudaStream_t st)
-{
-    const auto &a = *static_cast<const StepArgs<typename Prec<S>::R> *>(args);
-    switch (law) {
-    case LAW_SVK: return launch_step_t<S, LAW_SVK>(a, fuse, grid, st);
-    case LAW_NH: return launch_step_t<S, LAW_NH>(a, fuse, grid, st);
-    default: return launch_step_t<S, LAW_LOGNH>(a, fuse, grid, st);
-    }
-}
+// ---------------------------------------------------------------- dispatch
+#define TLV_DECLARE(NAME)                                                                                  \
+    cudaError_t launch_step_##NAME(int law, const void *args, bool fuse, int grid, cudaStream_t st);       \
+    cudaError_t launch_ghosts_##NAME(const EdgeArgs &a, int grid, cudaStream_t st);                       \
+    int step_blocks_##NAME(int law);
+TLV_DECLARE(f64)
+TLV_DECLARE(f32)
+TLV_DECLARE(bf16)
+TLV_DECLARE(f16)
 
 cudaError_t launch_step(int storage, int law, bool fuse, const void *args, int grid, cudaStream_t st)
 {
-    return with_storage(storage, [&](auto tag) {
-        return launch_step_law<decltype(tag)>(law, args, fuse, grid, st);
-    });
+    switch (storage) {
+    case STORE_F64: return launch_step_f64(law, args, fuse, grid, st);
+    case STORE_BF16: return launch_step_bf16(law, args, fuse, grid, st);
+    case STORE_F16: return launch_step_f16(law, args, fuse, grid, st);
+    default: return launch_step_f32(law, args, fuse, grid, st);
+    }
+}
+
+cudaError_t launch_ghosts(int storage, const EdgeArgs &a, int grid, cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+    switch (storage) {
+    case STORE_F64: return launch_ghosts_f64(a, grid, st);
+    case STORE_BF16: return launch_ghosts_bf16(a, grid, st);
+    case STORE_F16: return launch_ghosts_f16(a, grid, st);
+    default: return launch_ghosts_f32(a, grid, st);
+    }
+}
+
+int step_blocks_per_sm(int storage, int law)
+{
+    switch (storage) {
+    case STORE_F64: return step_blocks_f64(law);
+    case STORE_BF16: return step_blocks_bf16(law);
+    case STORE_F16: return step_blocks_f16(law);
+    default: return step_blocks_f32(law);
+    }
 }
 
 cudaError_t launch_edges(int storage, const EdgeArgs &a, int grid, cudaStream_t st)
@@ -370,39 +277,6 @@ cudaError_t launch_edges(int storage, const EdgeArgs &a, int grid, cudaStream_t 
     return with_storage(storage, [&](auto tag) {
         k_edges<decltype(tag)><<<grid, 128, 0, st>>>(a);
         return cudaGetLastError();
-    });
-}
-
-cudaError_t launch_ghosts(int storage, const EdgeArgs &a, int grid, cudaStream_t st)
-{
-    if (grid <= 0) return cudaSuccess;
-    return with_storage(storage, [&](auto tag) {
-        using S = decltype(tag);
-        switch (a.m.law) {
-        case LAW_SVK: k_ghosts<S, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
-        case LAW_NH: k_ghosts<S, LAW_NH><<<grid, 128, 0, st>>>(a); break;
-        default: k_ghosts<S, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
-        }
-        return cudaGetLastError();
-    });
-}
-
-int step_blocks_per_sm(int storage, int law)
-{
-    return with_storage(storage, [&](auto tag) {
-        using S = decltype(tag);
-        const void *fn;
-        if constexpr (sizeof(S) == 2)
-            fn = (law == LAW_SVK) ? (const void *)k_step16<S, LAW_SVK, STEP16_V, true>
-                 : (law == LAW_NH) ? (const void *)k_step16<S, LAW_NH, STEP16_V, true>
-                                   : (const void *)k_step16<S, LAW_LOGNH, STEP16_V, true>;
-        else
-            fn = (law == LAW_SVK) ? (const void *)k_step<S, LAW_SVK, 16 / sizeof(S), true>
-                 : (law == LAW_NH) ? (const void *)k_step<S, LAW_NH, 16 / sizeof(S), true>
-                                   : (const void *)k_step<S, LAW_LOGNH, 16 / sizeof(S), true>;
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
-        return n;
     });
 }
 

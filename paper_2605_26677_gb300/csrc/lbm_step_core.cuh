@@ -49,7 +49,7 @@ __device__ __forceinline__ void state_from_fstar(const T f0[6], const T f1[6], c
 // Eq. (12) equilibrium and Eq. (14) collision, in place on the four streamed
 // populations f[q][k] (offsets). Returns the velocity v^n.
 template <int LAW, typename T>
-__device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, T lam, T mu, bool real,
+__device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, const LawP<T> &m, bool real,
                                              unsigned &flags, T &v1, T &v2)
 {
     T U[6];
@@ -58,7 +58,7 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, T 
     U[0] += a.hdtb1;
     U[1] += a.hdtb2;
     T P11, P12, P21, P22, dJ;
-    piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], lam, mu, P11, P12, P21, P22, dJ);
+    piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], m, P11, P12, P21, P22, dJ);
     if (real) {
         if (!(dJ > T(-1))) flags |= ST_BAD_J;
         if (!(fabs(U[0]) + fabs(U[1]) + fabs(dJ) < T(INFINITY))) flags |= ST_NONFINITE;
@@ -87,7 +87,7 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, T 
 // column (plane 2, x = nx), with the edge data of the step that will pull
 // these values.
 template <int LAW, typename S, typename T>
-__device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, T lam, T mu,
+__device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, const LawP<T> &m,
                                             S *fout, unsigned &flags)
 {
     const int nx = a.L.nx, ny = a.L.ny;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const
         state_from_fstar(f[0], f[1], f[2], f[3], a.hdtb1, a.hdtb2, U);
         const double g = (a.gdev ? a.gdev[e] : a.g[e]) * (a.profile[e] ? a.profile[e][s] : 1.0);
         const double val[2] = {a.value[e][0] * g, a.value[e][1] * g};
-        edge_ghost<LAW, T>(e, a.kind[e], f[edge_dout(e)], U, val, a.c, lam, mu, out, flags);
+        edge_ghost<LAW, T>(e, a.kind[e], f[edge_dout(e)], U, val, a.c, m, out, flags);
         put(e, gx, gy, out);
     };
     if (a.kind[EDGE_BOTTOM] == BC_PERIODIC) {
@@ -154,12 +154,12 @@ __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> 
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(fout[(q * 6 + k) * a.L.plane + row + e]);
-        T lam = a.lam, mu = a.mu;
+        LawP<T> m{a.lam, a.mu, a.p2, a.p3};
         if (MATF) {
-            mu = a.mufield[(long long)y * a.L.upitch + x];
-            lam = a.lam_ratio * mu;
+            m.mu = a.mufield[(long long)y * a.L.upitch + x];
+            m.lam = a.lam_ratio * m.mu;
         }
-        node_ghosts<LAW, S, T>(fq, x, y, a, lam, mu, fout, flags);
+        node_ghosts<LAW, S, T>(fq, x, y, a, m, fout, flags);
     }
 }
 
@@ -227,8 +227,8 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) fq[q][k] = f[q][k][e];
-            collide_node<LAW, T>(fq, a, MATF ? a.lam_ratio * muv[e] : a.lam, muv[e], x0 + e < nx, flags, vel[0][e],
-                                 vel[1][e]);
+            const LawP<T> m{MATF ? a.lam_ratio * muv[e] : a.lam, muv[e], a.p2, a.p3};
+            collide_node<LAW, T>(fq, a, m, x0 + e < nx, flags, vel[0][e], vel[1][e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -386,7 +386,8 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) fq[q][k] = unpack16(w[q][k].w[e >> 1], e & 1, S());
-            collide_node<LAW, float>(fq, a, a.lam, a.mu, x0 + e < nx, flags, vel[0][e], vel[1][e]);
+            collide_node<LAW, float>(fq, a, LawP<float>{a.lam, a.mu, a.p2, a.p3}, x0 + e < nx, flags, vel[0][e],
+                                     vel[1][e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll

@@ -1,0 +1,178 @@
+// lbm_step_kernels.cuh -- the single-lattice step kernels (fused collide-
+// stream, Sec. 3.7) and the node-form ghost refresh, as templates over the
+// storage type and closure, with per-storage launch helpers. Each storage
+// type is instantiated in its own translation unit (lbm_step_<type>.cu).
+#pragma once
+#include "lbm_internal.h"
+#include "lbm_step_core.cuh"
+
+namespace tlv {
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
+    unsigned flags = 0;
+    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF>(a, task, lane, flags);
+    flags = __reduce_or_sync(FULL_MASK, flags);
+    if (flags && lane == 0) atomicOr(a.status, (int)flags);
+}
+
+template <typename S, int LAW, int V, bool FUSE>
+__global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int ntask = a.L.ny * ((a.L.nx + 32 * V - 1) / (32 * V));
+    unsigned flags = 0;
+    for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE>(a, task, lane, flags);
+    flags = __reduce_or_sync(FULL_MASK, flags);
+    if (flags && lane == 0) atomicOr(a.status, (int)flags);
+}
+
+// Ghost refresh in the node form (after initialization, a checkpoint load or
+// new edge data): the same values the fused step writes, from the stored
+// post-collision populations of the current buffer.
+template <typename S, int LAW>
+__global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
+{
+    using T = typename Prec<S>::R;
+    S *f = static_cast<S *>(a.f);
+    int e = 0;
+    while (e < 3 && (int)blockIdx.x >= a.blk_end[e]) ++e;
+    const int b0 = e ? a.blk_end[e - 1] : 0;
+    const int s = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x;
+    const int len = (e <= EDGE_RIGHT) ? a.L.ny : a.L.nx;
+    if (s >= len) return;
+    auto idx = [&](int q, int k, int x, int y) {
+        return (long long)(q * 6 + k) * a.L.plane + (long long)(y + 1) * a.L.pitch + a.L.xoff + x;
+    };
+    int xb, yb, gx, gy;
+    switch (e) {
+    case EDGE_LEFT: xb = 0; yb = s; gx = -1; gy = s; break;
+    case EDGE_RIGHT: xb = a.L.nx - 1; yb = s; gx = a.L.nx; gy = s; break;
+    case EDGE_BOTTOM: xb = s; yb = 0; gx = s; gy = -1; break;
+    default: xb = s; yb = a.L.ny - 1; gx = s; gy = a.L.ny; break;
+    }
+    const int d = edge_dmiss(e), md = edge_dout(e);
+    const EdgeDesc &E = a.e[e];
+    if (E.kind == BC_PERIODIC) {
+        const int sx = (e == EDGE_LEFT) ? a.L.nx - 1 : (e == EDGE_RIGHT) ? 0 : s;
+        const int sy = (e == EDGE_BOTTOM) ? a.L.ny - 1 : (e == EDGE_TOP) ? 0 : s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = f[idx(d, k, sx, sy)];
+        return;
+    }
+    T fq[4][6], U[6], fo[6], out[6];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(f[idx(q, k, xb, yb)]);
+    state_from_fstar(fq[0], fq[1], fq[2], fq[3], (T)a.hdtb1, (T)a.hdtb2, U);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fo[k] = fq[md][k];
+    double val[2];
+    edge_value(E, s, a.g[e], val);
+    unsigned flags = 0;
+    const LawP<T> m = law_cast<T>(law_at(a.m, (long long)yb * a.L.nx + xb));
+    edge_ghost<LAW, T>(e, E.kind, fo, U, val, (T)a.c, m, out, flags);
+    if (flags) atomicOr(a.status, (int)flags);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[idx(d, k, gx, gy)] = to_store<S>(out[k]);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename S, int LAW>
+static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
+{
+    if (a.mufield) {
+        // per-node material: FP64 and FP32 storage, SVK / NH / log-NH
+        if constexpr (sizeof(S) == 2 || LAW > LAW_LOGNH) {
+            return cudaErrorNotSupported;
+        } else {
+            if (fuse)
+                k_step<S, LAW, 16 / sizeof(S), true, true><<<grid, 128, 0, st>>>(a);
+            else
+                k_step<S, LAW, 16 / sizeof(S), false, true><<<grid, 128, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (sizeof(S) == 2) {
+        if (fuse)
+            k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);
+        else
+            k_step16<S, LAW, STEP16_V, false><<<grid, 128, 0, st>>>(a);
+    } else {
+        constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors
+        if (fuse)
+            k_step<S, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
+        else
+            k_step<S, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t launch_step_s(int law, const void *args, bool fuse, int grid, cudaStream_t st)
+{
+    const auto &a = *static_cast<const StepArgs<typename Prec<S>::R> *>(args);
+    switch (law) {
+    case LAW_SVK: return launch_step_t<S, LAW_SVK>(a, fuse, grid, st);
+    case LAW_NH: return launch_step_t<S, LAW_NH>(a, fuse, grid, st);
+    case LAW_LOGNH: return launch_step_t<S, LAW_LOGNH>(a, fuse, grid, st);
+    case LAW_MR: return launch_step_t<S, LAW_MR>(a, fuse, grid, st);
+    case LAW_YEOH: return launch_step_t<S, LAW_YEOH>(a, fuse, grid, st);
+    default: return launch_step_t<S, LAW_GENT>(a, fuse, grid, st);
+    }
+}
+
+template <typename S>
+static cudaError_t launch_ghosts_s(const EdgeArgs &a, int grid, cudaStream_t st)
+{
+    switch (a.m.law) {
+    case LAW_SVK: k_ghosts<S, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
+    case LAW_NH: k_ghosts<S, LAW_NH><<<grid, 128, 0, st>>>(a); break;
+    case LAW_LOGNH: k_ghosts<S, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
+    case LAW_MR: k_ghosts<S, LAW_MR><<<grid, 128, 0, st>>>(a); break;
+    case LAW_YEOH: k_ghosts<S, LAW_YEOH><<<grid, 128, 0, st>>>(a); break;
+    default: k_ghosts<S, LAW_GENT><<<grid, 128, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S, int LAW>
+static const void *step_fn()
+{
+    if constexpr (sizeof(S) == 2)
+        return (const void *)k_step16<S, LAW, STEP16_V, true>;
+    else
+        return (const void *)k_step<S, LAW, 16 / sizeof(S), true>;
+}
+
+template <typename S>
+static int step_blocks_s(int law)
+{
+    const void *fn = law == LAW_SVK ? step_fn<S, LAW_SVK>() : law == LAW_NH ? step_fn<S, LAW_NH>()
+                     : law == LAW_LOGNH ? step_fn<S, LAW_LOGNH>() : law == LAW_MR ? step_fn<S, LAW_MR>()
+                     : law == LAW_YEOH ? step_fn<S, LAW_YEOH>() : step_fn<S, LAW_GENT>();
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
+    return n;
+}
+
+// per-storage entry points, defined in lbm_step_<type>.cu
+#define TLV_STEP_ENTRY_POINTS(NAME, S)                                                                         \
+    cudaError_t launch_step_##NAME(int law, const void *args, bool fuse, int grid, cudaStream_t st)           \
+    {                                                                                                        \
+        return launch_step_s<S>(law, args, fuse, grid, st);                                                  \
+    }                                                                                                        \
+    cudaError_t launch_ghosts_##NAME(const EdgeArgs &a, int grid, cudaStream_t st)                           \
+    {                                                                                                        \
+        return launch_ghosts_s<S>(a, grid, st);                                                              \
+    }                                                                                                        \
+    int step_blocks_##NAME(int law) { return step_blocks_s<S>(law); }
+
+} // namespace tlv

@@ -6,7 +6,8 @@ import numpy as np
 
 from oracle import oracle as orc
 
-LAW_IDS = {"SVK": (0, orc.SVK), "NH": (1, orc.NH), "LOGNH": (2, orc.LOGNH)}
+LAW_IDS = {"SVK": (0, orc.SVK), "NH": (1, orc.NH), "LOGNH": (2, orc.LOGNH), "MR": (3, orc.MR),
+           "YEOH": (4, orc.YEOH), "GENT": (5, orc.GENT)}
 TIMEFN = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "sin_pulse": 3, "ricker": 4}
 KIND = {"periodic": 0, "velocity": 1, "traction": 2}
 
@@ -29,6 +30,10 @@ class Case:
     edges: dict = field(default_factory=dict)
     U0: np.ndarray = None
     u0: np.ndarray = None
+    params: tuple = None  # closure parameters when not (lam, mu)
+
+    def material(self):
+        return list(self.params) if self.params is not None else [self.lam, self.mu]
 
 
 def case_from_workload(w, steps=None):
@@ -73,7 +78,7 @@ def run_gpu(case: Case, storage):
     L = lbm.Lattice(case.nx, case.ny, dx=case.dx, c=case.c, omega=case.omega, storage=storage,
                     fb_mode=case.fb_mode)
     try:
-        lbm.lbm_set_material(L.ctx, LAW_IDS[case.law][0], [case.lam, case.mu])
+        lbm.lbm_set_material(L.ctx, LAW_IDS[case.law][0], case.material())
         lbm.lbm_set_body_force(L.ctx, *case.body)
         for e, (kind, val, tf, tp, prof) in case.edges.items():
             lbm.lbm_set_boundary(L.ctx, e, KIND[kind], val, TIMEFN[tf], tp, prof)
@@ -90,7 +95,7 @@ def run_gpu(case: Case, storage):
 
 def run_oracle(case: Case):
     O = orc.Lattice(case.nx, case.ny, case.dx, case.c, case.omega)
-    O.set_law(LAW_IDS[case.law][1], [case.lam, case.mu])
+    O.set_law(LAW_IDS[case.law][1], case.material())
     O.set_body_force(*case.body)
     O.set_fb_mode(case.fb_mode)
     for e, (kind, val, tf, tp, prof) in case.edges.items():

@@ -57,10 +57,13 @@ def test_call_order(lbm):
 
 def test_argument_checks(lbm):
     L = make(lbm)
-    with pytest.raises(lbm.LbmError, match="LBM_ERR_UNSUPPORTED"):
-        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_GENT, [1.0, 0.5, 10.0])
-    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
-        lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, -0.5])
+    for law, bad in ((lbm.LBM_LAW_GENT, [1.0, 0.5]), (lbm.LBM_LAW_GENT, [1.0, 0.5, -1.0]),
+                     (lbm.LBM_LAW_MR, [1.0, -0.1, 0.2]), (lbm.LBM_LAW_YEOH, [1.0, 0.5, 0.1]),
+                     (lbm.LBM_LAW_NH, [1.0, -0.5]), (7, [1.0, 0.5])):
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_set_material(L.ctx, law, bad)
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_GENT, [1.0, 0.5, 10.0])
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.0, 0.5])
     with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
         lbm.lbm_set_boundary(L.ctx, 4, lbm.LBM_BC_VELOCITY)
     with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):

@@ -141,6 +141,39 @@ def test_closures_bounded_logNH():
     check(case, F64)
 
 
+# Appendix A closures built on the isochoric invariants; lambda = 1.2 and a
+# small-strain shear modulus of 0.8 for each
+INVARIANT_LAWS = {"MR": (1.2, 0.3, 0.1), "YEOH": (1.2, 0.4, 0.05, 0.01), "GENT": (1.2, 0.8, 20.0)}
+
+
+@pytest.mark.parametrize("law", list(INVARIANT_LAWS))
+def test_invariant_closures_periodic(law):
+    nx, ny = 67, 29
+    U0 = smooth_field(nx, ny, seed=31, amp=0.08)
+    case = Case(nx, ny, 300, law=law, params=INVARIANT_LAWS[law], body=(1e-3, 0.0), U0=U0)
+    check(case, F64)
+    check(case, F32)
+
+
+@pytest.mark.parametrize("law", list(INVARIANT_LAWS))
+def test_invariant_closures_bounded(law):
+    # every edge a traction edge: the Newton solve for F^b and the
+    # second-order start both take the closure's tangent (dual numbers)
+    nx, ny = 50, 40
+    case = Case(nx, ny, 200, law=law, params=INVARIANT_LAWS[law], omega=1.9,
+                edges=edge_sets(nx, ny)["all_traction"], U0=smooth_field(nx, ny, seed=8, periodic=False))
+    check(case, F64)
+    check(case, F32)
+
+
+@pytest.mark.parametrize("law", list(INVARIANT_LAWS))
+@pytest.mark.parametrize("storage", [BF16, F16])
+def test_invariant_closures_16bit(law, storage):
+    nx, ny = 67, 29
+    U0 = smooth_field(nx, ny, seed=31, amp=0.08)
+    check(Case(nx, ny, 300, law=law, params=INVARIANT_LAWS[law], U0=U0), storage)
+
+
 # ---------------------------------------------------------------- initialization
 @pytest.mark.parametrize("order", [0, 2])
 @pytest.mark.parametrize("edges", ["periodic", "clamped_mixed"])
