@@ -8,8 +8,8 @@
 // Backward, segment by segment from the last: the states of the segment are
 // recomputed from its checkpoint into K - 1 slots (the step kernel, writing
 // u* and status into scratch), then for n = s1 - 1 .. s0 the adjoint kernel
-// maps a^{n+1} to a^n, the edge kernel completes a^n at the boundary and, at
-// a recorded step, the loss terms are added. Finally the init is transposed.
+// maps a^{n+1} to a^n (edges included) and, at a recorded step, the loss
+// terms are added. Finally the init is transposed.
 // K = ceil(sqrt(nsteps)) by default: about 2 sqrt(nsteps) stored states and
 // one recomputed forward step per backward step.
 #include <algorithm>
@@ -31,6 +31,7 @@ struct lbm_adjoint {
     std::vector<void *> ck;    // checkpoints f*^{kK}
     std::vector<void *> slot;  // recomputed states of one segment
     void *A[2] = {nullptr, nullptr};
+    void *tug[2] = {nullptr, nullptr};  // traction-edge cotangent of G, compute type, 4 planes (u* layout)
     void *ubar = nullptr;      // compute type, 2 planes (u* layout)
     double *gmu = nullptr;     // plane (u* layout)
     double *ustar_scr = nullptr;
@@ -80,15 +81,19 @@ lbm_status acuda(lbm_adjoint *a, cudaError_t e, const char *what)
 
 bool fp64(const lbm_adjoint *a) { return a->c->cfg.storage == LBM_STORE_F64; }
 
+// the step that maps a^{n+1} (buffers cur) to a^n (buffers cur ^ 1)
 template <typename T>
-AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, const void *ain, void *aout)
+AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, int cur)
 {
     const lbm_ctx *c = a->c;
     const double w = c->cfg.omega;
     AdjArgs<T> r;
     r.fin = fin;
-    r.ain = ain;
-    r.aout = aout;
+    r.ain = a->A[cur];
+    r.aout = a->A[cur ^ 1];
+    r.tug_in = static_cast<const T *>(a->tug[cur]);
+    r.tug_out = static_cast<T *>(a->tug[cur ^ 1]);
+    for (int e = 0; e < 4; ++e) r.kind[e] = c->edge[e].kind;
     r.mufield = static_cast<const T *>(c->d_muplane);
     r.ubar = static_cast<const T *>(a->ubar);
     r.gmu = a->gmu;
@@ -101,30 +106,6 @@ AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, const void *ain, void
     r.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
     r.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
     r.lam_ratio = (T)c->m.lam_ratio;
-    return r;
-}
-
-int ring_count(const Layout &L)
-{
-    const int rows = L.ny > 1 ? 2 : 1;
-    const int cols = L.nx > 1 ? 2 : 1;
-    return rows * L.nx + (L.ny > 2 ? (L.ny - 2) * cols : 0);
-}
-
-// the traction ghosts of f*^n carry the converged F^b of the forward
-template <typename T>
-FoldArgs<T> fold_args(const lbm_adjoint *a, const void *fin, void *aout)
-{
-    const lbm_ctx *c = a->c;
-    FoldArgs<T> r;
-    r.fin = fin;
-    r.aout = aout;
-    r.mufield = static_cast<const T *>(c->d_muplane);
-    r.gmu = a->gmu;
-    r.L = c->L;
-    for (int e = 0; e < 4; ++e) r.kind[e] = c->edge[e].kind;
-    r.lam_ratio = (T)c->m.lam_ratio;
-    r.count = ring_count(c->L);
     return r;
 }
 
@@ -184,19 +165,15 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
     return LBM_OK;
 }
 
-lbm_status adjoint_step(lbm_adjoint *a, const void *fin, const void *ain, void *aout, int grid)
+lbm_status adjoint_step(lbm_adjoint *a, const void *fin, int cur, int grid)
 {
     lbm_ctx *c = a->c;
     if (fp64(a)) {
-        const AdjArgs<double> r = adj_args<double>(a, fin, ain, aout);
+        const AdjArgs<double> r = adj_args<double>(a, fin, cur);
         AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
-        const FoldArgs<double> fr = fold_args<double>(a, fin, aout);
-        AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
     } else {
-        const AdjArgs<float> r = adj_args<float>(a, fin, ain, aout);
+        const AdjArgs<float> r = adj_args<float>(a, fin, cur);
         AK(a, launch_adj(c->cfg.storage, c->m.law, &r, grid, c->st));
-        const FoldArgs<float> fr = fold_args<float>(a, fin, aout);
-        AK(a, launch_adj_fold(c->cfg.storage, c->m.law, &fr, c->st));
     }
     return LBM_OK;
 }
@@ -209,6 +186,8 @@ void free_all(lbm_adjoint *a)
     a->slot.clear();
     cudaFree(a->A[0]);
     cudaFree(a->A[1]);
+    cudaFree(a->tug[0]);
+    cudaFree(a->tug[1]);
     cudaFree(a->ubar);
     cudaFree(a->gmu);
     cudaFree(a->ustar_scr);
@@ -262,6 +241,8 @@ lbm_status lbm_adjoint_create(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_eve
     for (auto &p : a->slot) alloc(&p, a->fbytes);
     alloc(&a->A[0], a->fbytes);
     alloc(&a->A[1], a->fbytes);
+    alloc(&a->tug[0], (size_t)4 * c->L.uplane * R);
+    alloc(&a->tug[1], (size_t)4 * c->L.uplane * R);
     alloc(&a->ubar, (size_t)2 * c->L.uplane * R);
     alloc((void **)&a->gmu, (size_t)c->L.uplane * sizeof(double));
     alloc((void **)&a->ustar_scr, (size_t)2 * c->L.uplane * sizeof(double));
@@ -344,6 +325,7 @@ lbm_status lbm_adjoint_set_loss(lbm_adjoint *a, int32_t nsens, const int32_t *se
 
 lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t order, double *loss)
 {
+    Range range_("lbm_adjoint_forward");
     if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
     if (!loss) return afail(a, LBM_ERR_ARG, "loss is NULL");
     if (a->nsens < 1) return afail(a, LBM_ERR_STATE, "lbm_adjoint_set_loss must come first");
@@ -391,6 +373,7 @@ lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t ord
 
 lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
 {
+    Range range_("lbm_adjoint_backward");
     if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
     if (!g_mu_dev || !g_v0_dev) return afail(a, LBM_ERR_ARG, "output pointers must be non-NULL");
     lbm_ctx *c = a->c;
@@ -401,6 +384,8 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
     AK(a, cudaEventRecord(a->ev[2], c->st));
     AK(a, cudaMemsetAsync(a->A[0], 0, a->fbytes, c->st));
     AK(a, cudaMemsetAsync(a->A[1], 0, a->fbytes, c->st));
+    AK(a, cudaMemsetAsync(a->tug[0], 0, (size_t)4 * c->L.uplane * R, c->st));
+    AK(a, cudaMemsetAsync(a->tug[1], 0, (size_t)4 * c->L.uplane * R, c->st));
     AK(a, cudaMemsetAsync(a->ubar, 0, (size_t)2 * c->L.uplane * R, c->st));
     AK(a, cudaMemsetAsync(a->gmu, 0, (size_t)c->L.uplane * sizeof(double), c->st));
     int cur = 0;
@@ -422,7 +407,7 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
             if (s != LBM_OK) return s;
         }
         for (long long n = s1 - 1; n >= s0; --n) {
-            s = adjoint_step(a, state(n), a->A[cur], a->A[cur ^ 1], grid);
+            s = adjoint_step(a, state(n), cur, grid);
             if (s != LBM_OK) return s;
             cur ^= 1;
             if (a->rec_at[(size_t)n] >= 0) {
@@ -455,6 +440,8 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
     ai.gmu = a->gmu;
     ai.gv0 = g_v0_dev;
     ai.ghat = a->ghat;
+    ai.tug = a->tug[cur];
+    for (int e = 0; e < 4; ++e) ai.kind[e] = c->edge[e].kind;
     AK(a, launch_adj_init(c->cfg.storage, ai, c->st));
     AK(a, launch_plane_to_compact(a->gmu, g_mu_dev, c->L, c->st));
     AK(a, cudaEventRecord(a->ev[3], c->st));

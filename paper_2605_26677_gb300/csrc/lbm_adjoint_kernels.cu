@@ -17,21 +17,77 @@
 // C has major symmetry (P derives from W), so A^T acts on F through the same
 // Jacobian action C : M as the forward (Eq. 8). P is linear in (lambda, mu)
 // for SVK, NH and log-NH, so dP/dmu along lambda = r mu is P(F; r, 1).
-// The pull becomes a push: a^n_q(x - e_q) = h_q(x). Pushes that leave the
-// domain land in the ghost cells; k_adj_fold then applies the transposed
-// edge rules there (velocity: a^n_{-d} = D h_d; traction: the same plus the
-// implicit-function-theorem derivative of the Newton solve for F^b, which
-// depends on the boundary node's tangential column and mu, evaluated at the
-// F^b the forward stored in the ghost cell; periodic: the ghost goes back to
-// the node it was copied from).
+// The pull becomes a push: a^n_q(x - e_q) = h_q(x). At the edges the same
+// kernel applies the transposed half-way rules (velocity: a^n_{-d} = D h_d;
+// traction: the same plus the implicit-function-theorem derivative of the
+// Newton solve for F^b, which depends on the boundary node's tangential
+// column and mu, evaluated at the F^b the forward stored in the ghost cell;
+// periodic: h_d goes back to the node it was copied from).
 #include "lbm_init_core.cuh"
 #include "lbm_step_core.cuh"
 
 namespace tlv {
 
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void ghost_cell(int e, int s, int nx, int ny, int &gx, int &gy)
+{
+    switch (e) {
+    case EDGE_LEFT: gx = -1; gy = s; break;
+    case EDGE_RIGHT: gx = nx; gy = s; break;
+    case EDGE_BOTTOM: gx = s; gy = -1; break;
+    default: gx = s; gy = ny; break;
+    }
+}
+
+__device__ __forceinline__ bool on_traction(const int kind[4], int x, int y, int nx, int ny)
+{
+    return (x == 0 && kind[EDGE_LEFT] == BC_TRACTION) || (x == nx - 1 && kind[EDGE_RIGHT] == BC_TRACTION) ||
+           (y == 0 && kind[EDGE_BOTTOM] == BC_TRACTION) || (y == ny - 1 && kind[EDGE_TOP] == BC_TRACTION);
+}
+
+// Traction edge e at a node with converged G^b (Sec. 3.6.2): the ghost's
+// F-part S_F = G^b / 2 got the cotangent hd[2..5]. The normal column n of G^b
+// solves r(n; t, mu) = N_a P_ia(G^b) - T_i = 0 with the tangential column t
+// taken from the node, so (implicit function theorem) dn/dt = -Jn^{-1} Jt and
+// dn/dmu = -Jn^{-1} dr/dmu. Adds the node's cotangent of G (tangential
+// column) to ug and returns the mu-cotangent in dmu.
+template <int LAW, typename T>
+__device__ __forceinline__ void traction_ift(int e, const T Gb[4], const T hd[6], T mu, T lam_ratio, T ug[4], T &dmu)
+{
+    const LawP<T> mp{lam_ratio * mu, mu, T(0), T(0)};
+    const int an = (e <= EDGE_RIGHT) ? 0 : 1, tc = 1 - an;
+    const T Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? T(-1) : T(1);
+    T Jn[2][2], Jt[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        T dF[4] = {T(0), T(0), T(0), T(0)}, dP[4];
+        dF[j * 2 + an] = T(1);
+        jvp_ofs<LAW, T>(Gb, dF, mp, dP);
+        Jn[0][j] = Na * dP[0 * 2 + an];
+        Jn[1][j] = Na * dP[1 * 2 + an];
+        dF[j * 2 + an] = T(0);
+        dF[j * 2 + tc] = T(1);
+        jvp_ofs<LAW, T>(Gb, dF, mp, dP);
+        Jt[0][j] = Na * dP[0 * 2 + an];
+        Jt[1][j] = Na * dP[1 * 2 + an];
+    }
+    const T Gbb[4] = {T(0.5) * hd[2], T(0.5) * hd[3], T(0.5) * hd[4], T(0.5) * hd[5]};
+    // z = -Jn^{-T} Gbb_normal
+    const T det = Jn[0][0] * Jn[1][1] - Jn[0][1] * Jn[1][0];
+    const T r0 = -Gbb[0 * 2 + an], r1 = -Gbb[1 * 2 + an];
+    const T z0 = (Jn[1][1] * r0 - Jn[1][0] * r1) / det;
+    const T z1 = (-Jn[0][1] * r0 + Jn[0][0] * r1) / det;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) ug[j * 2 + tc] += Gbb[j * 2 + tc] + z0 * Jt[0][j] + z1 * Jt[1][j];
+    T Pm[4], dJ;
+    piola_ofs<LAW, T>(Gb[0], Gb[1], Gb[2], Gb[3], LawP<T>{lam_ratio, T(1), T(0), T(0)}, Pm[0], Pm[1], Pm[2], Pm[3],
+                      dJ);
+    dmu = z0 * Na * Pm[0 * 2 + an] + z1 * Na * Pm[1 * 2 + an];
+}
+
 // ---------------------------------------------------------------- main
 template <typename S, int LAW, int VEC>
-__global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> a)
+__global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjArgs<typename Prec<S>::R> a)
 {
     using T = typename Prec<S>::R;
     using PK = Pack<S, VEC>;
@@ -52,7 +108,7 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
 
     for (int task = gw; task < ntask; task += nw) {
         int y, seg;
-        task_coords(task, nseg, y, seg);
+        task_coords(task, nseg, ny, y, seg);
         const int x0 = seg * segw + lane * VEC;
         const bool act = x0 < nx;
         const bool ld0 = x0 <= nx;
@@ -100,6 +156,19 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
                 for (int e = 0; e < VEC; ++e) h[q][k][e] = ld_r(v.v[e]);
             }
         const long long urow = (long long)y * a.L.upitch + x0;
+        // the traction edges' cotangent of U at their nodes, left by the
+        // previous (later-in-time) step for every q
+        if (act) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (x0 + e < nx && on_traction(a.kind, x0 + e, y, nx, ny))
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const T u = a.tug_in[m * a.L.uplane + urow + e];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) h[q][2 + m][e] += u;
+                    }
+        }
         PT mu = {}, ub0 = {}, ub1 = {};
         PD gm = {};
         if (act) {
@@ -137,13 +206,14 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
                 gm.v[e] -= a.wi2c_d * ((double)M[0] * Pm[0] + (double)M[1] * Pm[1] + (double)M[2] * Pm[2] +
                                        (double)M[3] * Pm[3]);
         }
-        if (act) *reinterpret_cast<PD *>(a.gmu + urow) = gm;
 
-        // pushes: a^n_q(x - e_q) = h_q(x)
+        // pushes: a^n_q(x - e_q) = h_q(x); what would leave the domain is
+        // handled by the edge rules below
         const bool full = act && x0 + VEC <= nx;
+        const bool ylo = (y == 0), yhi = (y == ny - 1);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            // q = 1 to row y - 1 and q = 3 to row y + 1 (the ghost rows at the ends)
+            // q = 1 to row y - 1 and q = 3 to row y + 1, inside the domain
             if (act) {
                 S *d1 = aout + (1 * 6 + k) * plane + row - pitch;
                 S *d3 = aout + (3 * 6 + k) * plane + row + pitch;
@@ -154,18 +224,18 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
                         o1.v[e] = to_store<S>(h[1][k][e]);
                         o3.v[e] = to_store<S>(h[3][k][e]);
                     }
-                    *reinterpret_cast<PK *>(d1) = o1;
-                    *reinterpret_cast<PK *>(d3) = o3;
+                    if (!ylo) *reinterpret_cast<PK *>(d1) = o1;
+                    if (!yhi) *reinterpret_cast<PK *>(d3) = o3;
                 } else {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e)
                         if (x0 + e < nx) {
-                            d1[e] = to_store<S>(h[1][k][e]);
-                            d3[e] = to_store<S>(h[3][k][e]);
+                            if (!ylo) d1[e] = to_store<S>(h[1][k][e]);
+                            if (!yhi) d3[e] = to_store<S>(h[3][k][e]);
                         }
                 }
             }
-            // q = 0 to column x - 1: position p = x0 + e takes h_0(p + 1)
+            // q = 0 to column x - 1: position p = x0 + e takes h_0(p + 1), p <= nx - 2
             {
                 const T nxt = __shfl_down_sync(FULL_MASK, h[0][k][0], 1);
                 S *d0 = aout + (0 * 6 + k) * plane + row;
@@ -183,15 +253,15 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
                         if (x0 + e <= nx - 2 && !(lane == 31 && e == VEC - 1))
                             d0[e] = to_store<S>(e < VEC - 1 ? h[0][k][e + 1] : nxt);
                 }
-                if (lane == 0 && act) d0[-1] = to_store<S>(h[0][k][0]);  // x0 - 1 (the ghost column for x0 = 0)
+                if (lane == 0 && act && x0 >= 1) d0[-1] = to_store<S>(h[0][k][0]);  // the previous segment's last position
             }
-            // q = 2 to column x + 1: position p = x0 + e takes h_2(p - 1)
+            // q = 2 to column x + 1: position p = x0 + e takes h_2(p - 1), 1 <= p <= nx - 1
             {
                 const T prv = __shfl_up_sync(FULL_MASK, h[2][k][VEC - 1], 1);
                 S *d2 = aout + (2 * 6 + k) * plane + row;
                 bool all = true;
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) all = all && (x0 + e >= 1) && (x0 + e <= nx) && !(lane == 0 && e == 0);
+                for (int e = 0; e < VEC; ++e) all = all && (x0 + e >= 1) && (x0 + e <= nx - 1) && !(lane == 0 && e == 0);
                 if (all) {
                     PK o;
 #pragma unroll
@@ -200,159 +270,76 @@ __global__ void __launch_bounds__(128) k_adj(const AdjArgs<typename Prec<S>::R> 
                 } else {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e)
-                        if (x0 + e >= 1 && x0 + e <= nx && !(lane == 0 && e == 0))
+                        if (x0 + e >= 1 && x0 + e <= nx - 1 && !(lane == 0 && e == 0))
                             d2[e] = to_store<S>(e == 0 ? prv : h[2][k][e - 1]);
                 }
-                // the next segment's first position (or the ghost column x = nx)
-                if (lane == 31 && x0 + VEC - 1 < nx) d2[VEC] = to_store<S>(h[2][k][VEC - 1]);
+                if (lane == 31 && x0 + VEC <= nx - 1) d2[VEC] = to_store<S>(h[2][k][VEC - 1]);  // the next segment's first
             }
         }
-    }
-}
 
-// ---------------------------------------------------------------- edges
-__device__ __forceinline__ void ring_node(int t, int nx, int ny, int &x, int &y)
-{
-    const int rows = ny > 1 ? 2 : 1;
-    if (t < rows * nx) {
-        x = t % nx;
-        y = (t < nx) ? 0 : ny - 1;
-        return;
-    }
-    t -= rows * nx;
-    const int side = ny - 2;
-    x = (t < side) ? 0 : nx - 1;
-    y = 1 + (t < side ? t : t - side);
-}
-
-__device__ __forceinline__ void ghost_cell(int e, int s, int nx, int ny, int &gx, int &gy)
-{
-    switch (e) {
-    case EDGE_LEFT: gx = -1; gy = s; break;
-    case EDGE_RIGHT: gx = nx; gy = s; break;
-    case EDGE_BOTTOM: gx = s; gy = -1; break;
-    default: gx = s; gy = ny; break;
-    }
-}
-
-// One thread per boundary-ring node. Every value the node's edges need is
-// loaded first, the transposed rules are applied in registers, and the node's
-// cells are stored last, so the loads are independent and issue together
-// (a thread walks at most four edges; its destination planes are distinct).
-template <typename S, int LAW>
-__global__ void __launch_bounds__(128) k_adj_fold(const FoldArgs<typename Prec<S>::R> a)
-{
-    using T = typename Prec<S>::R;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.count) return;
-    const int nx = a.L.nx, ny = a.L.ny;
-    int x, y;
-    ring_node(t, nx, ny, x, y);
-    const S *__restrict__ fin = static_cast<const S *>(a.fin);
-    S *__restrict__ aout = static_cast<S *>(a.aout);
-    auto idx = [&](int q, int k, int xx, int yy) {
-        return (long long)(q * 6 + k) * a.L.plane + (long long)(yy + 1) * a.L.pitch + a.L.xoff + xx;
-    };
-    bool on[4];
-    on[EDGE_LEFT] = x == 0;
-    on[EDGE_RIGHT] = x == nx - 1;
-    on[EDGE_BOTTOM] = y == 0;
-    on[EDGE_TOP] = y == ny - 1;
-    bool traction = false;
-    for (int e = 0; e < 4; ++e) traction = traction || (on[e] && a.kind[e] == BC_TRACTION);
-
-    // loads
-    T src[4][6];       // per edge: the ghost value it takes its cotangent from
-    T gb[4][4];        // per traction edge: the forward's G^b
-    T cur[4][4];       // the node's F-components in every plane (for the broadcast)
-    int dest[4];       // destination plane per edge, -1 if none
-    for (int e = 0; e < 4; ++e) {
-        dest[e] = -1;
-        if (!on[e]) continue;
-        const int s = (e <= EDGE_RIGHT) ? y : x;
-        int gx, gy;
-        if (a.kind[e] == BC_PERIODIC) {
-            // this node's outgoing population was copied into the opposite
-            // edge's ghost cell; its cotangent comes back from there
-            const int o = e ^ 1;  // LEFT <-> RIGHT, BOTTOM <-> TOP
-            dest[e] = edge_dmiss(o);
-            ghost_cell(o, s, nx, ny, gx, gy);
-            for (int k = 0; k < 6; ++k) src[e][k] = ld_r(aout[idx(dest[e], k, gx, gy)]);
-            continue;
+        // Edge rules, transposed (Eqs. 23-25), at the lane's boundary nodes.
+        // The node x_b pulled f_d(x_b) = D f*_{-d}(x_b) + S_d(U^n(x_b)) (or, on a
+        // periodic edge, the opposite node's f*_d), so its h_d goes to
+        // a^n_{-d}(x_b) with D (or back to that opposite node). A traction
+        // edge adds the implicit-function derivative of F^b, which reaches
+        // every q of x_b through U^n = sum_q f*^n_q: its F-part is left in
+        // tug_out for the next step to add, and its mu-part goes to dL/dmu.
+        // No other thread writes the cells written here.
+        if (act && (ylo || yhi || x0 == 0 || x0 + VEC >= nx)) {
+            T ug[VEC][4];
+            bool tr[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                tr[e] = false;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) ug[e][m] = T(0);
+            }
+#pragma unroll
+            for (int ed = 0; ed < 4; ++ed) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int x = x0 + e;
+                    if (x >= nx) continue;
+                    const bool on = (ed == EDGE_LEFT) ? x == 0 : (ed == EDGE_RIGHT) ? x == nx - 1 : (ed == EDGE_BOTTOM) ? ylo : yhi;
+                    if (!on) continue;
+                    const int d = edge_dmiss(ed), md = edge_dout(ed);
+                    T hd[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) hd[k] = h[d][k][e];
+                    if (a.kind[ed] == BC_PERIODIC) {
+                        const int tx = (ed == EDGE_LEFT) ? nx - 1 : (ed == EDGE_RIGHT) ? 0 : x;
+                        const int ty = (ed == EDGE_BOTTOM) ? ny - 1 : (ed == EDGE_TOP) ? 0 : y;
+                        const long long cell = (long long)(ty + 1) * pitch + a.L.xoff + tx;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) aout[(d * 6 + k) * plane + cell] = to_store<S>(hd[k]);
+                        continue;
+                    }
+                    const T sv = (a.kind[ed] == BC_VELOCITY) ? T(-1) : T(1);  // D on (v1, v2); -sv on F
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) aout[(md * 6 + k) * plane + row + e] = to_store<S>((k < 2 ? sv : -sv) * hd[k]);
+                    if (a.kind[ed] != BC_TRACTION) continue;
+                    tr[e] = true;
+                    // the forward stored ghost = -f*_{-d} + G^b / 2 on the F-components
+                    int gx, gy;
+                    ghost_cell(ed, (ed <= EDGE_RIGHT) ? y : x, nx, ny, gx, gy);
+                    const long long gcell = (long long)(gy + 1) * pitch + a.L.xoff + gx;
+                    T Gb[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        Gb[m] = T(2) * (ld_r(fin[(d * 6 + 2 + m) * plane + gcell]) + ld_r(fin[(md * 6 + 2 + m) * plane + row + e]));
+                    T dmu;
+                    traction_ift<LAW, T>(ed, Gb, hd, mu.v[e], a.lam_ratio, ug[e], dmu);
+                    gm.v[e] += (double)dmu;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (tr[e])
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) a.tug_out[m * a.L.uplane + urow + e] = ug[e][m];
         }
-        const int d = edge_dmiss(e), md = edge_dout(e);
-        dest[e] = md;
-        ghost_cell(e, s, nx, ny, gx, gy);
-        for (int k = 0; k < 6; ++k) src[e][k] = ld_r(aout[idx(d, k, gx, gy)]);
-        if (a.kind[e] == BC_TRACTION)
-            // the forward stored ghost = -f*_{-d} + G^b / 2 on the F-components
-            for (int m = 0; m < 4; ++m)
-                gb[e][m] = T(2) * (ld_r(fin[idx(d, 2 + m, gx, gy)]) + ld_r(fin[idx(md, 2 + m, x, y)]));
+        if (act) *reinterpret_cast<PD *>(a.gmu + urow) = gm;
     }
-    T mu = T(0);
-    double gm0 = 0.0;
-    if (traction) {
-        for (int q = 0; q < 4; ++q)
-            for (int m = 0; m < 4; ++m) cur[q][m] = ld_r(aout[idx(q, 2 + m, x, y)]);
-        mu = a.mufield[(long long)y * a.L.upitch + x];
-        gm0 = a.gmu[(long long)y * a.L.upitch + x];
-    }
-
-    // transposed rules
-    T out[4][6];
-    bool isdest[4] = {false, false, false, false};
-    T UG[4] = {T(0), T(0), T(0), T(0)};
-    double gm = 0.0;
-    for (int e = 0; e < 4; ++e) {
-        if (dest[e] < 0) continue;
-        isdest[dest[e]] = true;
-        if (a.kind[e] == BC_PERIODIC) {
-            for (int k = 0; k < 6; ++k) out[dest[e]][k] = src[e][k];
-            continue;
-        }
-        const T sv = (a.kind[e] == BC_VELOCITY) ? T(-1) : T(1);  // D on (v1, v2); -sv on F
-        for (int k = 0; k < 6; ++k) out[dest[e]][k] = (k < 2 ? sv : -sv) * src[e][k];
-        if (a.kind[e] != BC_TRACTION) continue;
-        // S_F = G^b / 2 with G^b from N_a P_ia(F^b) = T_i (Sec. 3.6.2)
-        const LawP<T> mp{a.lam_ratio * mu, mu, T(0), T(0)};
-        const int an = (e <= EDGE_RIGHT) ? 0 : 1, tc = 1 - an;
-        const T Na = (e == EDGE_LEFT || e == EDGE_BOTTOM) ? T(-1) : T(1);
-        T Jn[2][2], Jt[2][2];
-        for (int j = 0; j < 2; ++j) {
-            T dF[4] = {T(0), T(0), T(0), T(0)}, dP[4];
-            dF[j * 2 + an] = T(1);
-            jvp_ofs<LAW, T>(gb[e], dF, mp, dP);
-            Jn[0][j] = Na * dP[0 * 2 + an];
-            Jn[1][j] = Na * dP[1 * 2 + an];
-            dF[j * 2 + an] = T(0);
-            dF[j * 2 + tc] = T(1);
-            jvp_ofs<LAW, T>(gb[e], dF, mp, dP);
-            Jt[0][j] = Na * dP[0 * 2 + an];
-            Jt[1][j] = Na * dP[1 * 2 + an];
-        }
-        const T Gbb[4] = {T(0.5) * src[e][2], T(0.5) * src[e][3], T(0.5) * src[e][4], T(0.5) * src[e][5]};
-        // z = -Jn^{-T} Gbb_normal
-        const T det = Jn[0][0] * Jn[1][1] - Jn[0][1] * Jn[1][0];
-        const T r0 = -Gbb[0 * 2 + an], r1 = -Gbb[1 * 2 + an];
-        const T z0 = (Jn[1][1] * r0 - Jn[1][0] * r1) / det;
-        const T z1 = (-Jn[0][1] * r0 + Jn[0][0] * r1) / det;
-        for (int j = 0; j < 2; ++j) UG[j * 2 + tc] += Gbb[j * 2 + tc] + z0 * Jt[0][j] + z1 * Jt[1][j];
-        T Pm[4], dJ;
-        piola_ofs<LAW, T>(gb[e][0], gb[e][1], gb[e][2], gb[e][3], LawP<T>{a.lam_ratio, T(1), T(0), T(0)}, Pm[0],
-                          Pm[1], Pm[2], Pm[3], dJ);
-        gm += (double)(z0 * Na * Pm[0 * 2 + an]) + (double)(z1 * Na * Pm[1 * 2 + an]);
-    }
-
-    // stores; U^n(x_b) = sum_q f*^n_q - (dt/2) B, so the traction cotangent
-    // of U reaches every q of the node
-    for (int q = 0; q < 4; ++q) {
-        if (isdest[q]) {
-            for (int k = 0; k < 6; ++k) aout[idx(q, k, x, y)] = to_store<S>(out[q][k] + (k >= 2 ? UG[k - 2] : T(0)));
-        } else if (traction) {
-            for (int m = 0; m < 4; ++m) aout[idx(q, 2 + m, x, y)] = to_store<S>(cur[q][m] + UG[m]);
-        }
-    }
-    if (traction) a.gmu[(long long)y * a.L.upitch + x] = gm0 + gm;
 }
 
 // ---------------------------------------------------------------- sensors
@@ -428,6 +415,11 @@ __global__ void __launch_bounds__(128) k_adj_init(const AdjInitArgs a)
         double h[4][6], Sa[6], bX[6], bY[6];
         for (int q = 0; q < 4; ++q)
             for (int k = 0; k < 6; ++k) h[q][k] = (double)ld_r(a0[pidx(ia.L, q, k, x, y)]);
+        if (on_traction(a.kind, x, y, nx, ny))
+            for (int m = 0; m < 4; ++m) {
+                const double u = (double)static_cast<const T *>(a.tug)[m * ia.L.uplane + ui];
+                for (int q = 0; q < 4; ++q) h[q][2 + m] += u;
+            }
         for (int k = 0; k < 6; ++k) {
             Sa[k] = (h[0][k] + h[2][k]) + (h[1][k] + h[3][k]);
             bX[k] = h[0][k] - h[2][k];
@@ -592,28 +584,6 @@ int adj_blocks_per_sm(int storage, int law)
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
     return n;
-}
-
-template <typename S>
-static cudaError_t launch_fold_s(int law, const void *args, cudaStream_t st)
-{
-    using T = typename Prec<S>::R;
-    const auto &a = *static_cast<const FoldArgs<T> *>(args);
-    if (a.count <= 0) return cudaSuccess;
-    const int grid = (a.count + 127) / 128;
-    switch (law) {
-    case LAW_SVK: k_adj_fold<S, LAW_SVK><<<grid, 128, 0, st>>>(a); break;
-    case LAW_NH: k_adj_fold<S, LAW_NH><<<grid, 128, 0, st>>>(a); break;
-    default: k_adj_fold<S, LAW_LOGNH><<<grid, 128, 0, st>>>(a); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adj_fold(int storage, int law, const void *args, cudaStream_t st)
-{
-    if (storage == STORE_F64) return launch_fold_s<double>(law, args, st);
-    if (storage == STORE_F32) return launch_fold_s<float>(law, args, st);
-    return cudaErrorNotSupported;
 }
 
 cudaError_t launch_adj_record(int storage, const RecordArgs &a, cudaStream_t st)

@@ -641,6 +641,7 @@ static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
 
 lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t order)
 {
+    Range range_("lbm_init");
     lbm_status s = init_checks(c, U0, order);
     if (s != LBM_OK) return s;
     CK(c, cudaSetDevice(c->cfg.device));
@@ -662,6 +663,7 @@ lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t orde
 
 lbm_status lbm_init_device(lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
 {
+    Range range_("lbm_init_device");
     lbm_status s = init_checks(c, U0_dev, order);
     if (s != LBM_OK) return s;
     CK(c, cudaSetDevice(c->cfg.device));
@@ -670,6 +672,7 @@ lbm_status lbm_init_device(lbm_ctx *c, const double *U0_dev, const double *u0_de
 
 lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
 {
+    Range range_("lbm_step");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
@@ -694,6 +697,7 @@ lbm_status lbm_sync(lbm_ctx *c)
 
 lbm_status lbm_read_state(lbm_ctx *c, double *U, double *P, double *t)
 {
+    Range range_("lbm_read_state");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (!U) return fail(c, LBM_ERR_ARG, "U is NULL");
@@ -716,6 +720,7 @@ lbm_status lbm_read_state_device(lbm_ctx *c, double *U_dev, double *P_dev)
 
 lbm_status lbm_read_displacement(lbm_ctx *c, double *u)
 {
+    Range range_("lbm_read_displacement");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (!u) return fail(c, LBM_ERR_ARG, "u is NULL");
@@ -742,6 +747,7 @@ lbm_status lbm_read_cauchy(lbm_ctx *c, double *sigma)
 
 lbm_status lbm_diagnostics(lbm_ctx *c, double out[10])
 {
+    Range range_("lbm_diagnostics");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
@@ -762,6 +768,7 @@ lbm_status lbm_diagnostics(lbm_ctx *c, double out[10])
 
 lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
 {
+    Range range_("lbm_save");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (!bytes) return fail(c, LBM_ERR_ARG, "bytes is NULL");
@@ -806,6 +813,7 @@ lbm_status lbm_save(lbm_ctx *c, void *buf, size_t *bytes)
 
 lbm_status lbm_load(lbm_ctx *c, const void *buf, size_t bytes)
 {
+    Range range_("lbm_load");
     lbm_status s = check_ready(c);
     if (s != LBM_OK) return s;
     if (!buf || bytes < sizeof(SaveHeader)) return fail(c, LBM_ERR_ARG, "buffer too small");

@@ -569,6 +569,7 @@ lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t size_class, int32_t vec)
 
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
 {
+    Range range_("lbm_batch_tune");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "null batch");
     if (reps < 1) return bfail(b, LBM_ERR_ARG, "reps must be >= 1");
     BK(b, cudaSetDevice(b->device));
@@ -649,6 +650,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps, int32_t graph_steps, int32_t *member_status)
 {
+    Range range_("lbm_batch_step");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "null batch");
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps must be >= 0");
     if (graph_steps < 0 || (graph_steps & 1) || graph_steps > TIME_CHUNK)

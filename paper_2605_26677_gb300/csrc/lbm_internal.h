@@ -5,6 +5,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 #include "lbm_device.cuh"
@@ -40,6 +41,15 @@ struct lbm_ctx {
 
 
 namespace tlv {
+
+// NVTX range around a library call, shown by Nsight tools on their timeline
+// (header-only NVTX 3: without an attached tool the calls return at once)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // lbm_step.cu
 // fuse: the step kernel also writes the next step's ghost cells (node form)
@@ -101,21 +111,13 @@ struct AdjArgs {
     const T *mufield;   // u* plane layout
     const T *ubar;      // dL/du*, two planes, u* plane layout
     double *gmu;        // dL/dmu accumulator, u* plane layout
+    const T *tug_in;    // cotangent of G at traction-edge nodes for every q of a^{n+1} (4 planes)
+    T *tug_out;         // the same for a^n
     Layout L;
+    int kind[4];        // edge kinds
     T one_m_omega, wq, wi2c, dtT;  // 1 - w, w/4, w/(2c), dt
     T hdtb1, hdtb2, lam_ratio;
     double wi2c_d;
-};
-template <typename T>
-struct FoldArgs {
-    const void *fin;
-    void *aout;
-    const T *mufield;
-    double *gmu;
-    Layout L;
-    int kind[4];
-    T lam_ratio;
-    int count;                 // boundary ring nodes
 };
 struct RecordArgs {
     const void *f;
@@ -143,11 +145,12 @@ struct AdjInitArgs {
     double *gmu;        // plane
     double *gv0;        // 2N compact (output)
     double *ghat;       // 4N compact scratch
+    const void *tug;    // traction-edge cotangent of G for every q of a^0 (compute type, 4 planes)
+    int kind[4];
 };
 cudaError_t launch_adj(int storage, int law, const void *args, int grid, cudaStream_t st);
 int adj_blocks_per_sm(int storage, int law);
 int adj_vec_for(int storage);  // nodes per lane of the adjoint kernel
-cudaError_t launch_adj_fold(int storage, int law, const void *args, cudaStream_t st);
 cudaError_t launch_adj_record(int storage, const RecordArgs &a, cudaStream_t st);
 cudaError_t launch_adj_inject(int storage, const void *args, cudaStream_t st);
 cudaError_t launch_adj_init(int storage, const AdjInitArgs &a, cudaStream_t st);

@@ -121,14 +121,18 @@ __device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const
     }
 }
 
-// Task order shared by both step kernels: (row, segment) with the segments of
-// row y rotated by y -- with a warp count that is a multiple of the number of
-// segments, an unrotated order would give every edge segment (and its Newton
-// solves) to the same few warps.
-__device__ __forceinline__ void task_coords(int task, int nseg, int &y, int &seg)
+// Task order shared by the step kernels: (row, segment), rows in the order
+// 0, ny - 1, 1, 2, ..., ny - 2, and the segments of row y rotated by y. The
+// two edge rows, whose every lane runs edge rules (traction Newton solves),
+// come first, so that their longer tasks overlap the later rounds of the
+// persistent grid instead of forming its tail; without the rotation, a warp
+// count that is a multiple of the segments per row would hand every edge
+// segment of the side edges to the same few warps.
+__device__ __forceinline__ void task_coords(int task, int nseg, int ny, int &y, int &seg)
 {
-    y = task / nseg;
-    seg = (task - y * nseg + y) % nseg;
+    const int r = task / nseg;
+    y = (r == 0 || ny < 2) ? r : (r == 1 ? ny - 1 : r - 1);
+    seg = (task - r * nseg + y) % nseg;
 }
 
 // After a lane has stored its nodes, the ghost cells its boundary nodes are
@@ -181,7 +185,7 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
     S *__restrict__ fout = static_cast<S *>(a.fout);
     {
         int y, seg;
-        task_coords(task, nseg, y, seg);
+        task_coords(task, nseg, a.L.ny, y, seg);
         const int x0 = seg * segw + lane * VEC;
         const bool act = x0 < nx;   // lane owns at least one real node
         const bool ld0 = x0 <= nx;  // lane's vector holds a real node or the right ghost column
@@ -334,7 +338,7 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
 
     {
         int y, seg;
-        task_coords(task, nseg, y, seg);
+        task_coords(task, nseg, a.L.ny, y, seg);
         const int x0 = seg * segw + lane * V;
         const bool act = x0 < nx;
         const bool ld0 = x0 <= nx;
