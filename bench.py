@@ -74,6 +74,17 @@ def dist_setup(args):
     return rank, ws, dist
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -214,10 +225,7 @@ def run_ours(args, rank, ws, dist):
     clocks = clk.summary()
     bpn = lbm.lbm_bytes_per_node_update(L.ctx)
     L.close()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     value = N * args.steps * ws / (ms_max * 1e-3) / 1e6
 
     # roofline of the bulk kernel from its own event-timed launches
