@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-forms", action="store_true", help="skip the FP64 and 8192^2 side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    p.add_argument("--form", choices=["batch", "adjoint"], default=None,
+    p.add_argument("--form", choices=["batch", "adjoint", "bf16"], default=None,
                    help="run only this side measurement and print its JSON (profiling); not a bench line")
     p.add_argument("--form-steps", type=int, default=None, help="steps of the --form run")
     return p.parse_args()
@@ -490,6 +490,17 @@ def main():
 
         if args.form == "batch":
             line = {"form": "batch", **batch_form(lbm, torch, peaks()[0], args.form_steps or 200)}
+        elif args.form == "bf16":
+            from synth import clamped_specimen
+
+            w = clamped_specimen()
+            U0, u0 = w.fields()
+            L = setup_ctx(lbm, w, lbm.LBM_STORE_BF16, U0, u0)
+            k = args.form_steps or 200
+            ms, prof = timed_steps(lbm, torch, L, k, 5, None)
+            L.close()
+            line = {"form": "bf16", "value": w.nx * w.ny * k / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": k,
+                    "kernel_us": prof["step"][1] / max(prof["step"][0], 1) * 1e3}
         else:
             line = {"form": "adjoint", **adjoint_form(lbm, torch, args.form_steps or 2000, all_states=False)}
     elif args.impl == "reference":
