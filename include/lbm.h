@@ -88,9 +88,11 @@ typedef enum { LBM_LAW_SVK = 0, LBM_LAW_NH = 1, LBM_LAW_LOGNH = 2, LBM_LAW_MR = 
  *   SIN2_RAMP: {T}: sin^2(pi t / (2T)) for t < T, else 1      (shape of Eq. 33)
  *   SIN_PULSE: {T}: sin(pi t / T) for t < T, else 0            (shape of Eq. 35)
  *   RICKER: {s, t0, t_end}: 2/(sqrt(3s) pi^(1/4)) (1 - z^2) exp(-z^2/2),
- *           z = (t - t0)/s, for t <= t_end, else 0              (Sec. 5.4) */
+ *           z = (t - t0)/s, for t <= t_end, else 0              (Sec. 5.4)
+ *   TABLE: -: the edge's table of lbm_set_boundary_table (a measured or
+ *          otherwise given load history) */
 typedef enum { LBM_T_CONST = 0, LBM_T_LINEAR_RAMP = 1, LBM_T_SIN2_RAMP = 2, LBM_T_SIN_PULSE = 3,
-               LBM_T_RICKER = 4 } lbm_timefn;
+               LBM_T_RICKER = 4, LBM_T_TABLE = 5 } lbm_timefn;
 
 /* Tangential column of the traction-edge boundary deformation gradient F^b
  * (Sec. 3.6.2; the normal column always solves P(F^b) N = T by Newton):
@@ -148,6 +150,9 @@ lbm_status lbm_set_material(lbm_ctx *ctx, int32_t law, const double *params, int
  * applies from the next step on. Copied; waits for the upload. Contexts with
  * a field cannot join a batch. */
 lbm_status lbm_set_material_field(lbm_ctx *ctx, int32_t law, const double *mu, double lam_ratio);
+/* The same from a device array mu_dev (N doubles on the context's GPU, read
+ * on the context's stream; checked on the device). Synchronises. */
+lbm_status lbm_set_material_field_device(lbm_ctx *ctx, int32_t law, const double *mu_dev, double lam_ratio);
 
 /* Uniform body acceleration b = (b1, b2) of Eq. (1); B = (b1, b2, 0, 0, 0, 0)
  * enters the state recovery (Eq. 10) and the collision source (Eq. 14).
@@ -162,6 +167,13 @@ lbm_status lbm_set_body_force(lbm_ctx *ctx, double b1, double b2);
  * steps; the new data applies from the next step. Default: periodic. */
 lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t edge, int32_t bc, const double value[2],
                             int32_t timefn, const double tparams[4], const double *profile);
+
+/* Tabulated time function of an edge (used when its timefn is LBM_T_TABLE):
+ * g(t) piecewise linear through the n points (t[i], g[i]) (host arrays,
+ * copied; t strictly increasing), constant before the first and after the
+ * last. Stepping an edge with LBM_T_TABLE and no table is LBM_ERR_STATE. May
+ * be changed between steps; waits for the context's queued work. */
+lbm_status lbm_set_boundary_table(lbm_ctx *ctx, int32_t edge, int32_t n, const double *t, const double *g);
 
 /* Initial state (Sec. 3.4 and 3.5). U0 (host, 6N) holds v0 and F0 = I + Grad u0;
  * u0 (host, 2N, NULL = 0) the initial displacement. order 0 starts from the

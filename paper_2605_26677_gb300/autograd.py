@@ -19,7 +19,7 @@ class _Misfit(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mu, v0, owner):
         o = owner
-        lbm.lbm_set_material_field(o.lattice.ctx, o.law, mu.detach().cpu().numpy(), o.lam_ratio)
+        lbm.lbm_set_material_field_device(o.lattice.ctx, o.law, mu.detach().contiguous(), o.lam_ratio)
         U0 = torch.zeros((6, o.ny, o.nx), dtype=torch.float64, device=mu.device)
         U0[2] = 1.0
         U0[5] = 1.0

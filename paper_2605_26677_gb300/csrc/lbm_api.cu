@@ -4,6 +4,7 @@
 // lbm_device.cuh), the FP64 displacement accumulator u*, a device status word,
 // a device step counter and a small diagnostics scratch area. Every device
 // operation is enqueued on the stream given at creation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +56,9 @@ bool yper(const lbm_ctx *c) { return c->edge[EDGE_BOTTOM].kind == BC_PERIODIC; }
 // Edge pairing and minimum sizes (one-sided three-point stencils need 3 nodes).
 lbm_status check_edges(lbm_ctx *c)
 {
+    for (int e = 0; e < 4; ++e)
+        if (c->edge[e].kind != BC_PERIODIC && c->edge[e].timefn == TF_TABLE && c->tab_t[e].empty())
+            return fail(c, LBM_ERR_STATE, "an edge with LBM_T_TABLE has no table (lbm_set_boundary_table)");
     if ((c->edge[EDGE_LEFT].kind == BC_PERIODIC) != (c->edge[EDGE_RIGHT].kind == BC_PERIODIC))
         return fail(c, LBM_ERR_ARG, "left and right edges must both be periodic or both non-periodic");
     if ((c->edge[EDGE_BOTTOM].kind == BC_PERIODIC) != (c->edge[EDGE_TOP].kind == BC_PERIODIC))
@@ -86,10 +90,23 @@ lbm_status sync_status(lbm_ctx *c)
 // ghosts the next step pulls, whose edge data belong to t^{n+1} + dt/2
 // (Eq. 23). One out-of-line function serves the single and batched paths so
 // that both see the same rounding.
+static double edge_time(const lbm_ctx *c, int e, double t)
+{
+    if (c->edge[e].timefn != TF_TABLE) return timefn(c->edge[e].timefn, c->edge[e].tp, t);
+    // piecewise linear through (t_i, g_i), constant beyond the first and last point
+    const std::vector<double> &ts = c->tab_t[e], &gs = c->tab_g[e];
+    if (ts.empty()) return 0.0;
+    if (t <= ts.front()) return gs.front();
+    if (t >= ts.back()) return gs.back();
+    const size_t i = (size_t)(std::upper_bound(ts.begin(), ts.end(), t) - ts.begin());  // ts[i-1] <= t < ts[i]
+    const double w = (t - ts[i - 1]) / (ts[i] - ts[i - 1]);
+    return gs[i - 1] + w * (gs[i] - gs[i - 1]);
+}
+
 __attribute__((noinline)) double tlv::ctx_time_factor(const lbm_ctx *c, int e, long long step)
 {
     const double th = ((double)step + 1.5) * c->dt;
-    return timefn(c->edge[e].timefn, c->edge[e].tp, th);
+    return edge_time(c, e, th);
 }
 
 namespace {
@@ -151,7 +168,7 @@ EdgeArgs edge_args(const lbm_ctx *c, int cur)
     a.yper = yper(c);
     // the ghosts of the stored f*^n serve the pull of step n + 1: t^n + dt/2
     const double th = ((double)c->step + 0.5) * c->dt;
-    for (int e = 0; e < 4; ++e) a.g[e] = timefn(c->edge[e].timefn, c->edge[e].tp, th);
+    for (int e = 0; e < 4; ++e) a.g[e] = edge_time(c, e, th);
     a.status = c->d_status;
     return a;
 }
@@ -507,7 +524,7 @@ lbm_status lbm_set_material(lbm_ctx *c, int32_t law, const double *params, int32
     return set_step_grid(c);
 }
 
-lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, double lam_ratio)
+static lbm_status field_checks(lbm_ctx *c, int32_t law, const void *mu, double lam_ratio)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH)
@@ -516,22 +533,34 @@ lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, dou
         return fail(c, LBM_ERR_UNSUPPORTED, "material fields need FP64 or FP32 storage");
     if (!mu) return fail(c, LBM_ERR_ARG, "mu is NULL");
     if (!is_finite(lam_ratio) || !(lam_ratio + 2.0 > 0.0)) return fail(c, LBM_ERR_ARG, "lam_ratio must be finite and > -2");
+    return LBM_OK;
+}
+
+// Copy the field (host or device source) into new buffers, then replace the
+// old field; on an error the context keeps its old material.
+static lbm_status install_field(lbm_ctx *c, int32_t law, const double *mu, bool from_device, double lam_ratio,
+                                double mumax)
+{
     const size_t N = (size_t)c->L.nx * c->L.ny;
-    double mumax = 0.0;
-    for (size_t n = 0; n < N; ++n) {
-        if (!is_finite(mu[n]) || !(mu[n] > 0.0)) return fail(c, LBM_ERR_ARG, "mu must be finite and > 0 at every node");
-        mumax = std::max(mumax, mu[n]);
-    }
-    CK(c, cudaSetDevice(c->cfg.device));
-    CK(c, cudaStreamSynchronize(c->st));  // queued steps may still read the old field
-    drop_material_field(c);
     const size_t pbytes = (size_t)c->L.uplane * (c->cfg.storage == LBM_STORE_F64 ? 8 : 4);
-    CK(c, cudaMalloc((void **)&c->d_mufield, N * sizeof(double)));
-    CK(c, cudaMalloc(&c->d_muplane, pbytes));
-    CK(c, cudaMemsetAsync(c->d_muplane, 0, pbytes, c->st));
-    CK(c, cudaMemcpyAsync(c->d_mufield, mu, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    CK(c, launch_mu_plane(c->cfg.storage, c->d_mufield, c->d_muplane, c->L, c->st));
-    CK(c, cudaStreamSynchronize(c->st));
+    double *field = nullptr;
+    void *plane = nullptr;
+    cudaError_t e = cudaMalloc((void **)&field, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&plane, pbytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plane, 0, pbytes, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(field, mu, N * sizeof(double), from_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            c->st);
+    if (e == cudaSuccess) e = launch_mu_plane(c->cfg.storage, field, plane, c->L, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // also: queued steps are done with the old field
+    if (e != cudaSuccess) {
+        cudaFree(field);
+        cudaFree(plane);
+        return cuda_fail(c, e, "material field upload");
+    }
+    drop_material_field(c);
+    c->d_mufield = field;
+    c->d_muplane = plane;
     c->m.law = law;
     c->m.p2 = c->m.p3 = 0.0;
     c->m.mufield = c->d_mufield;
@@ -542,6 +571,31 @@ lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, dou
     c->have_material = true;
     c->ghosts_dirty = true;
     return set_step_grid(c);
+}
+
+lbm_status lbm_set_material_field(lbm_ctx *c, int32_t law, const double *mu, double lam_ratio)
+{
+    lbm_status s = field_checks(c, law, mu, lam_ratio);
+    if (s != LBM_OK) return s;
+    const size_t N = (size_t)c->L.nx * c->L.ny;
+    double mumax = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        if (!is_finite(mu[n]) || !(mu[n] > 0.0)) return fail(c, LBM_ERR_ARG, "mu must be finite and > 0 at every node");
+        mumax = std::max(mumax, mu[n]);
+    }
+    CK(c, cudaSetDevice(c->cfg.device));
+    return install_field(c, law, mu, false, lam_ratio, mumax);
+}
+
+lbm_status lbm_set_material_field_device(lbm_ctx *c, int32_t law, const double *mu_dev, double lam_ratio)
+{
+    lbm_status s = field_checks(c, law, mu_dev, lam_ratio);
+    if (s != LBM_OK) return s;
+    CK(c, cudaSetDevice(c->cfg.device));
+    double stats[3];  // min, max, number of non-finite values
+    CK(c, launch_field_stats(mu_dev, (long long)c->L.nx * c->L.ny, stats, c->st));
+    if (stats[2] > 0.0 || !(stats[0] > 0.0)) return fail(c, LBM_ERR_ARG, "mu must be finite and > 0 at every node");
+    return install_field(c, law, mu_dev, true, lam_ratio, stats[1]);
 }
 
 
@@ -561,7 +615,7 @@ lbm_status lbm_set_boundary(lbm_ctx *c, int32_t edge, int32_t bc, const double v
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (edge < 0 || edge > 3) return fail(c, LBM_ERR_ARG, "edge must be 0..3");
     if (bc < LBM_BC_PERIODIC || bc > LBM_BC_TRACTION) return fail(c, LBM_ERR_ARG, "unknown boundary kind");
-    if (timefn < LBM_T_CONST || timefn > LBM_T_RICKER) return fail(c, LBM_ERR_ARG, "unknown time function");
+    if (timefn < LBM_T_CONST || timefn > LBM_T_TABLE) return fail(c, LBM_ERR_ARG, "unknown time function");
     EdgeDesc d{};
     d.kind = bc;
     d.timefn = timefn;
@@ -589,6 +643,23 @@ lbm_status lbm_set_boundary(lbm_ctx *c, int32_t edge, int32_t bc, const double v
         d.profile = nullptr;
     }
     c->edge[edge] = d;
+    c->ghosts_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_boundary_table(lbm_ctx *c, int32_t edge, int32_t n, const double *t, const double *g)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
+    if (edge < 0 || edge > 3) return fail(c, LBM_ERR_ARG, "edge must be 0..3");
+    if (n < 1 || !t || !g) return fail(c, LBM_ERR_ARG, "a table needs n >= 1 points");
+    for (int i = 0; i < n; ++i) {
+        if (!is_finite(t[i]) || !is_finite(g[i])) return fail(c, LBM_ERR_ARG, "table entries must be finite");
+        if (i > 0 && !(t[i] > t[i - 1])) return fail(c, LBM_ERR_ARG, "table times must increase strictly");
+    }
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->st));  // steps already queued used the old table on the host
+    c->tab_t[edge].assign(t, t + n);
+    c->tab_g[edge].assign(g, g + n);
     c->ghosts_dirty = true;
     return LBM_OK;
 }

@@ -284,4 +284,61 @@ cudaError_t launch_mu_plane(int storage, const double *mu, void *plane, const La
     return cudaGetLastError();
 }
 
+constexpr int STATS_BLOCKS = 256;
+
+__global__ void __launch_bounds__(256) k_field_stats(const double *v, long long n, double *partial)
+{
+    __shared__ double smin[256], smax[256], sbad[256];
+    double lo = DBL_MAX, hi = -DBL_MAX, bad = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = v[i];
+        if (!isfinite(x)) {
+            bad += 1.0;
+        } else {
+            lo = fmin(lo, x);
+            hi = fmax(hi, x);
+        }
+    }
+    smin[threadIdx.x] = lo;
+    smax[threadIdx.x] = hi;
+    sbad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+            sbad[threadIdx.x] += sbad[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[3 * blockIdx.x] = smin[0];
+        partial[3 * blockIdx.x + 1] = smax[0];
+        partial[3 * blockIdx.x + 2] = sbad[0];
+    }
+}
+
+cudaError_t launch_field_stats(const double *v, long long n, double out[3], cudaStream_t st)
+{
+    double *partial = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&partial, 3 * STATS_BLOCKS * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_field_stats<<<STATS_BLOCKS, 256, 0, st>>>(v, n, partial);
+    double h[3 * STATS_BLOCKS];
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, partial, sizeof h, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(partial, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    out[0] = DBL_MAX;
+    out[1] = -DBL_MAX;
+    out[2] = 0.0;
+    for (int b = 0; b < STATS_BLOCKS; ++b) {
+        out[0] = fmin(out[0], h[3 * b]);
+        out[1] = fmax(out[1], h[3 * b + 1]);
+        out[2] += h[3 * b + 2];
+    }
+    return cudaSuccess;
+}
+
 } // namespace tlv

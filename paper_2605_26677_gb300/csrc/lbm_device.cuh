@@ -78,7 +78,7 @@ __host__ auto with_storage(int storage, Fn fn)
 enum { EDGE_LEFT = 0, EDGE_RIGHT = 1, EDGE_BOTTOM = 2, EDGE_TOP = 3 };
 enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_TRACTION = 2 };
 enum { LAW_SVK = 0, LAW_NH = 1, LAW_LOGNH = 2, LAW_MR = 3, LAW_YEOH = 4, LAW_GENT = 5 };
-enum { TF_CONST = 0, TF_LINEAR_RAMP = 1, TF_SIN2_RAMP = 2, TF_SIN_PULSE = 3, TF_RICKER = 4 };
+enum { TF_CONST = 0, TF_LINEAR_RAMP = 1, TF_SIN2_RAMP = 2, TF_SIN_PULSE = 3, TF_RICKER = 4, TF_TABLE = 5 };
 enum { FB_NODE = 0, FB_EXTRAP2 = 1 };
 enum { ST_BAD_J = 1, ST_NEWTON = 2, ST_NONFINITE = 4 };
 

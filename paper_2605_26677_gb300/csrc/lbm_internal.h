@@ -35,6 +35,7 @@ struct lbm_ctx {
     std::string err;
     bool prof = false;
     std::vector<cudaEvent_t> ev_step, ev_edge; // start/stop pairs
+    std::vector<double> tab_t[4], tab_g[4];  // per-edge tabulated g(t) (LBM_T_TABLE)
     double *d_mufield = nullptr;  // per-node mu, compact FP64 (N), or nullptr
     void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
 };
@@ -77,6 +78,8 @@ struct InitArgs {
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st);
 // per-node mu (compact FP64) -> compute-type plane in the u* layout (zero padding)
 cudaError_t launch_mu_plane(int storage, const double *mu, void *plane, const Layout &L, cudaStream_t st);
+// min, max and the number of non-finite values of a device array (host out[3]; synchronises)
+cudaError_t launch_field_stats(const double *v, long long n, double out[3], cudaStream_t st);
 
 struct ReadArgs {
     const void *f;      // current post-collision populations

@@ -22,13 +22,14 @@ LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = range(4)
 LBM_EDGE_LEFT, LBM_EDGE_RIGHT, LBM_EDGE_BOTTOM, LBM_EDGE_TOP = range(4)
 LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_TRACTION = range(3)
 LBM_LAW_SVK, LBM_LAW_NH, LBM_LAW_LOGNH, LBM_LAW_MR, LBM_LAW_YEOH, LBM_LAW_GENT = range(6)
-LBM_T_CONST, LBM_T_LINEAR_RAMP, LBM_T_SIN2_RAMP, LBM_T_SIN_PULSE, LBM_T_RICKER = range(5)
+LBM_T_CONST, LBM_T_LINEAR_RAMP, LBM_T_SIN2_RAMP, LBM_T_SIN_PULSE, LBM_T_RICKER, LBM_T_TABLE = range(6)
 LBM_FB_NODE, LBM_FB_EXTRAP2 = range(2)
 
 # every symbol include/lbm.h declares
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "lbm_set_material_field",
+           "lbm_set_material_field_device",
            "lbm_set_body_force",
-           "lbm_set_boundary", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
+           "lbm_set_boundary", "lbm_set_boundary_table", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
            "lbm_read_state", "lbm_read_state_device", "lbm_read_displacement", "lbm_read_displacement_device",
            "lbm_read_cauchy", "lbm_diagnostics", "lbm_save", "lbm_load", "lbm_info", "lbm_profile",
            "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc",
@@ -76,8 +77,10 @@ _lib.lbm_last_error.argtypes = [_ctx]
 _lib.lbm_last_error.restype = C.c_char_p
 _lib.lbm_set_material.argtypes = [_ctx, C.c_int32, _dp, C.c_int32]
 _lib.lbm_set_material_field.argtypes = [_ctx, C.c_int32, _dp, C.c_double]
+_lib.lbm_set_material_field_device.argtypes = [_ctx, C.c_int32, C.c_void_p, C.c_double]
 _lib.lbm_set_body_force.argtypes = [_ctx, C.c_double, C.c_double]
 _lib.lbm_set_boundary.argtypes = [_ctx, C.c_int32, C.c_int32, _dp, C.c_int32, _dp, _dp]
+_lib.lbm_set_boundary_table.argtypes = [_ctx, C.c_int32, C.c_int32, _dp, _dp]
 _lib.lbm_init.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 _lib.lbm_init_device.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 _lib.lbm_step.argtypes = [_ctx, C.c_int64]
@@ -216,6 +219,11 @@ def lbm_set_material_field(ctx, law, mu, lam_ratio):
     _check(ctx, _lib.lbm_set_material_field(ctx, law, m.ctypes.data_as(_dp), float(lam_ratio)))
 
 
+def lbm_set_material_field_device(ctx, law, mu_dev, lam_ratio):
+    """mu_dev: (ny, nx) float64 CUDA tensor."""
+    _check(ctx, _lib.lbm_set_material_field_device(ctx, law, _dev(mu_dev, ctx.nx * ctx.ny), float(lam_ratio)))
+
+
 def lbm_set_body_force(ctx, b1, b2):
     _check(ctx, _lib.lbm_set_body_force(ctx, b1, b2))
 
@@ -229,6 +237,15 @@ def lbm_set_boundary(ctx, edge, bc, value=(0.0, 0.0), timefn=LBM_T_CONST, tparam
     _check(ctx, _lib.lbm_set_boundary(ctx, edge, bc, v.ctypes.data_as(_dp), timefn,
                                       None if tp is None else tp.ctypes.data_as(_dp),
                                       None if pr is None else pr.ctypes.data_as(_dp)))
+
+
+def lbm_set_boundary_table(ctx, edge, t, g):
+    """Piecewise-linear g(t) through (t[i], g[i]) for an edge with LBM_T_TABLE."""
+    t = np.ascontiguousarray(t, dtype=np.float64).ravel()
+    g = np.ascontiguousarray(g, dtype=np.float64).ravel()
+    if t.size != g.size:
+        raise ValueError("t and g need the same length")
+    _check(ctx, _lib.lbm_set_boundary_table(ctx, edge, t.size, t.ctypes.data_as(_dp), g.ctypes.data_as(_dp)))
 
 
 def lbm_init(ctx, U0, u0=None, order=2):

@@ -211,6 +211,30 @@ def test_autograd_function(lbm):
     assert np.array_equal(v0.grad.cpu().numpy(), gv0)
 
 
+def test_material_field_from_device_equals_host(lbm):
+    import torch
+
+    w = small_workload(steps=30)
+    U0, _ = w.fields()
+    out = []
+    for dev in (False, True):
+        L = gpu_ctx(lbm, w, F32)
+        if dev:
+            lbm.lbm_set_material_field_device(L.ctx, 1, torch.from_numpy(w.params["mu"]).cuda(), 2.0)
+        lbm.lbm_init(L.ctx, U0)
+        lbm.lbm_step(L.ctx, w.steps)
+        out.append(lbm.lbm_read_state(L.ctx, want_P=False)[0])
+        L.close()
+    assert np.array_equal(out[0], out[1])
+    L = gpu_ctx(lbm, w, F32)
+    for bad in (-1.0, np.nan, 0.0):
+        mu = w.params["mu"].copy()
+        mu[3, 5] = bad
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_set_material_field_device(L.ctx, 1, torch.from_numpy(mu).cuda(), 2.0)
+    L.close()
+
+
 def test_adjoint_argument_errors(lbm):
     w = small_workload(steps=10)
     L = lbm.Lattice(w.nx, w.ny, c=w.c, storage=F32)

@@ -280,6 +280,53 @@ def test_edge_data_changed_between_steps(storage, fb_mode):
         assert v <= (tol["U"] if k == "U" else tol["group"]), (k, v, errs)
 
 
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_tabulated_time_function(storage):
+    """LBM_T_TABLE: a piecewise-linear load history on the right (traction)
+    edge. The oracle has no tables; it gets the same edge data written out
+    step by step (its explicit per-node edge data, the value times the
+    table interpolated by numpy at t^n + dt/2)."""
+    from oracle import oracle as orc
+    from paper_2605_26677_gb300 import lbm
+    from tests.cases import KIND, TIMEFN, group_errors
+
+    nx, ny, steps = 70, 40, 120
+    E = edge_sets(nx, ny)["clamped_mixed"]
+    U0 = smooth_field(nx, ny, seed=14, periodic=False)
+    value = (0.04, -0.01)
+    tt = np.array([0.0, 3.0, 7.5, 12.0, 20.0])
+    gg = np.array([0.0, 1.0, 0.4, -0.3, 0.1])
+    L = lbm.Lattice(nx, ny, omega=1.9, storage=storage)
+    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [1.5, 0.75])
+    for e, (k, v, tf, tp, pr) in E.items():
+        lbm.lbm_set_boundary(L.ctx, e, KIND[k], v, TIMEFN[tf], tp, pr)
+    lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, value, lbm.LBM_T_TABLE)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        lbm.lbm_init(L.ctx, U0)  # the table is missing
+    lbm.lbm_set_boundary_table(L.ctx, 1, tt, gg)
+    lbm.lbm_init(L.ctx, U0)
+    lbm.lbm_step(L.ctx, steps)
+    U, P, _ = lbm.lbm_read_state(L.ctx)
+    u = lbm.lbm_read_displacement(L.ctx)
+    L.close()
+    O = orc.Lattice(nx, ny, 1.0, 5.0, 1.9)
+    O.set_law(orc.NH, [1.5, 0.75])
+    for e, (k, v, tf, tp, pr) in E.items():
+        O.set_edge(e, KIND[k], v, TIMEFN[tf], tp if tp is not None else (0, 0, 0, 0), pr)
+    O.set_edge(1, orc.TRACTION, value)
+    O.init(U0)
+    for n in range(steps):
+        g = np.interp((n + 0.5) * O.dt, tt, gg)
+        O.set_edge_data(1, np.array([[value[0] * g] * ny, [value[1] * g] * ny]))
+        O.step(1)
+    Uo, Po, So = O.state()
+    errs = group_errors({"U": U, "P": P, "u": u, "sigma": So}, {"U": Uo, "P": Po, "u": O.displacement(), "sigma": So})
+    tol = TOL[storage]
+    for k in ("v", "F-I", "P", "u"):
+        assert errs[k] <= tol["group"], (k, errs)
+    assert errs["U"] <= tol["U"], errs
+
+
 @pytest.mark.parametrize("storage", [F64, F32, F16, BF16])
 def test_precision_error_vs_oracle_fourier(storage):
     """Error of each storage precision against the FP64 oracle on the 16-mode
