@@ -73,6 +73,7 @@ lbm_status map_flags(lbm_ctx *c, int flags)
     if (flags & ST_NONFINITE) return fail(c, LBM_ERR_NONFINITE, "the state became non-finite");
     if (flags & ST_BAD_J) return fail(c, LBM_ERR_NONPOSITIVE_J, "a node reached J = det F <= 0");
     if (flags & ST_NEWTON) return fail(c, LBM_ERR_NEWTON, "a traction-edge Newton solve did not converge");
+    if (flags & ST_STALL) return fail(c, LBM_ERR_CUDA, "a step kernel's wait for its bulk copies exceeded its time bound");
     return LBM_OK;
 }
 

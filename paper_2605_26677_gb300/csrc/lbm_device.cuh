@@ -80,7 +80,7 @@ enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_TRACTION = 2 };
 enum { LAW_SVK = 0, LAW_NH = 1, LAW_LOGNH = 2, LAW_MR = 3, LAW_YEOH = 4, LAW_GENT = 5 };
 enum { TF_CONST = 0, TF_LINEAR_RAMP = 1, TF_SIN2_RAMP = 2, TF_SIN_PULSE = 3, TF_RICKER = 4, TF_TABLE = 5 };
 enum { FB_NODE = 0, FB_EXTRAP2 = 1 };
-enum { ST_BAD_J = 1, ST_NEWTON = 2, ST_NONFINITE = 4 };
+enum { ST_BAD_J = 1, ST_NEWTON = 2, ST_NONFINITE = 4, ST_STALL = 8 };  // ST_STALL: a bounded wait gave up
 
 struct Layout {
     long long plane;  // elements per population plane

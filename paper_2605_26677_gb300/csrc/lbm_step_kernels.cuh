@@ -5,6 +5,7 @@
 #pragma once
 #include "lbm_internal.h"
 #include "lbm_step_core.cuh"
+#include "lbm_step16_staged.cuh"
 
 namespace tlv {
 template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
@@ -101,6 +102,8 @@ static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fu
         }
     }
     if constexpr (sizeof(S) == 2) {
+        cudaError_t e;
+        if (launch_step16_staged<S, LAW>(a, fuse, grid, st, e)) return e;
         if (fuse)
             k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);
         else
@@ -143,24 +146,32 @@ static cudaError_t launch_ghosts_s(const EdgeArgs &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// resident blocks per SM of the step kernel that will run (fused form)
 template <typename S, int LAW>
-static const void *step_fn()
+static int step_blocks_t()
 {
-    if constexpr (sizeof(S) == 2)
-        return (const void *)k_step16<S, LAW, STEP16_V, true>;
-    else
-        return (const void *)k_step<S, LAW, 16 / sizeof(S), true>;
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(S) == 2) {
+        if (!step16_staged_blocks<S, LAW>(n, e))
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step16<S, LAW, STEP16_V, true>, 128, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, LAW, 16 / sizeof(S), true>, 128, 0);
+    }
+    return e == cudaSuccess ? n : 0;
 }
 
 template <typename S>
 static int step_blocks_s(int law)
 {
-    const void *fn = law == LAW_SVK ? step_fn<S, LAW_SVK>() : law == LAW_NH ? step_fn<S, LAW_NH>()
-                     : law == LAW_LOGNH ? step_fn<S, LAW_LOGNH>() : law == LAW_MR ? step_fn<S, LAW_MR>()
-                     : law == LAW_YEOH ? step_fn<S, LAW_YEOH>() : step_fn<S, LAW_GENT>();
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, 0) != cudaSuccess) n = 0;
-    return n;
+    switch (law) {
+    case LAW_SVK: return step_blocks_t<S, LAW_SVK>();
+    case LAW_NH: return step_blocks_t<S, LAW_NH>();
+    case LAW_LOGNH: return step_blocks_t<S, LAW_LOGNH>();
+    case LAW_MR: return step_blocks_t<S, LAW_MR>();
+    case LAW_YEOH: return step_blocks_t<S, LAW_YEOH>();
+    default: return step_blocks_t<S, LAW_GENT>();
+    }
 }
 
 // per-storage entry points, defined in lbm_step_<type>.cu
