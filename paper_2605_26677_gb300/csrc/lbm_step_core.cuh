@@ -68,16 +68,30 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, co
     // f^eq_q = U/4 + (1/2c)(i Phi_X + j Phi_Y)
     const T PhiX[6] = {-P11, -P21, -U[0], T(0), -U[1], T(0)};
     const T PhiY[6] = {-P12, -P22, T(0), -U[0], T(0), -U[1]};
+    // f* = (1 - omega) f + omega f^eq + dt (2 - omega) w B. The structural
+    // zeros (Phi_X of F12 and F22, Phi_Y of F11 and F21, the source beyond
+    // the velocity components) are skipped at compile time: under IEEE rules
+    // the compiler may not drop a product with or a sum of a zero itself.
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
+        const bool hx = (k != 3 && k != 5), hy = (k != 2 && k != 4);
         const T qU = a.quarter * U[k];
-        const T fx = a.inv2c * PhiX[k], fy = a.inv2c * PhiY[k];
-        const T src = (k == 0) ? a.src1 : (k == 1) ? a.src2 : T(0);
-        // f* = (1 - omega) f + omega f^eq + dt (2 - omega) w B
-        f[0][k] = a.one_m_omega * f[0][k] + a.omega * (qU + fx) + src;
-        f[2][k] = a.one_m_omega * f[2][k] + a.omega * (qU - fx) + src;
-        f[1][k] = a.one_m_omega * f[1][k] + a.omega * (qU + fy) + src;
-        f[3][k] = a.one_m_omega * f[3][k] + a.omega * (qU - fy) + src;
+        const T fx = hx ? a.inv2c * PhiX[k] : T(0), fy = hy ? a.inv2c * PhiY[k] : T(0);
+        T g0 = a.one_m_omega * f[0][k] + a.omega * (hx ? qU + fx : qU);
+        T g2 = a.one_m_omega * f[2][k] + a.omega * (hx ? qU - fx : qU);
+        T g1 = a.one_m_omega * f[1][k] + a.omega * (hy ? qU + fy : qU);
+        T g3 = a.one_m_omega * f[3][k] + a.omega * (hy ? qU - fy : qU);
+        if (k < 2) {
+            const T src = (k == 0) ? a.src1 : a.src2;
+            g0 += src;
+            g2 += src;
+            g1 += src;
+            g3 += src;
+        }
+        f[0][k] = g0;
+        f[2][k] = g2;
+        f[1][k] = g1;
+        f[3][k] = g3;
     }
 }
 
