@@ -209,16 +209,17 @@ __global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const 
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
 
-// Which 16-bit step kernel runs: the staged one (default; one stage per
-// warp, four blocks per SM: 188 us per step against 190 us with two stages
-// at three blocks per SM and 198 us for the register kernel, BF16, 4096 x
-// 2048 clamped specimen) or the register kernel ("LBM_STEP16=regs" in the
-// environment). Read once per process.
+// Which 16-bit step kernel runs: the register kernel (default: faster or
+// equal on every lattice measured but one; BF16 us per step, register /
+// staged: 2896^2 periodic 187.0 / 194.4, 6144 x 2048 clamped 273.9 / 281.5,
+// 8192^2 periodic 1391.5 / 1591.8, 4096 x 2048 clamped 192.3 / 185.0) or
+// the staged kernel ("LBM_STEP16=staged" in the environment). Read once per
+// process.
 static int step16_stages()
 {
     static const int ns = [] {
         const char *v = std::getenv("LBM_STEP16");
-        return (v && !std::strcmp(v, "regs")) ? 0 : 1;
+        return (v && !std::strcmp(v, "staged")) ? 1 : 0;
     }();
     return ns;
 }

@@ -1,8 +1,8 @@
-"""The 16-bit step kernels against each other: the staged kernel (rows moved
-into shared memory by bulk asynchronous copies; the default) and the
-register kernel (LBM_STEP16=regs in the environment) run the same tasks
-through the same per-node arithmetic, so after any number of steps their
-states, displacements and diagnostics agree bit for bit. The kernel is
+"""The 16-bit step kernels against each other: the register kernel (the
+default) and the staged kernel (rows moved into shared memory by bulk
+asynchronous copies; LBM_STEP16=staged in the environment) run the same
+tasks through the same per-node arithmetic, so after any number of steps
+their states, displacements and diagnostics agree bit for bit. The kernel is
 chosen once per process, so each one runs in a child process over the same
 cases; their agreement with the oracle is the 16-bit part of
 test_gpu_parity, which runs the default kernel.
@@ -72,8 +72,8 @@ def built():
 
 
 def test_staged_and_register_kernels_bit_identical(tmp_path):
-    ref = run_variant(tmp_path, "regs")
-    got = run_variant(tmp_path, None)
+    ref = run_variant(tmp_path, None)
+    got = run_variant(tmp_path, "staged")
     assert set(got) == set(ref)
     for k in ref:
         assert np.all(np.isfinite(ref[k])), k
