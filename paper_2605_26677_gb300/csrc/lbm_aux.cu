@@ -1,8 +1,11 @@
 // lbm_aux.cu -- initialization, read-out and diagnostics kernels of the TL
-// vectorial D2Q4x6 LBM. All of them compute in FP64 whatever the storage.
+// vectorial D2Q4x6 LBM. Read-out and diagnostics compute in FP64 whatever the
+// storage; the initialization computes in FP64 for FP64 storage and in FP32
+// otherwise (u* always in FP64).
 #include <cfloat>
 
 #include "lbm_init_core.cuh"
+#include <type_traits>
 
 namespace tlv {
 
@@ -11,35 +14,39 @@ namespace tlv {
 template <typename T>
 __global__ void __launch_bounds__(128) k_init(const InitArgs a)
 {
+    using R = typename std::conditional<sizeof(T) == 8, double, float>::type;  // compute type
     const int nx = a.L.nx, ny = a.L.ny;
     const long long N = (long long)nx * ny;
     T *fout = static_cast<T *>(a.fout);
-    const double c = a.c, dt = a.dt;
+    const double dt = a.dt;
+    const R c = (R)a.c, w = (R)a.omega;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
-        double f[4][6];
-        const LawP<double> m = law_at(a.m, n);
-        if (!init_node(a, x, y, m, f)) atomicOr(a.status, ST_BAD_J);
-        // step-0 collision (Eqs. 10, 12, 14)
-        double Un[6], dJ;
-        for (int k = 0; k < 6; ++k) Un[k] = f[0][k] + f[1][k] + f[2][k] + f[3][k];
-        Un[0] += 0.5 * dt * a.b1;
-        Un[1] += 0.5 * dt * a.b2;
-        const double Gn[4] = {Un[2] - 1.0, Un[3], Un[4], Un[5] - 1.0};
-        double Pn[4], feq[4][6];
-        piola_any(a.m.law, Gn, m, Pn, dJ);
-        feq_full(Un, Pn, c, feq);
-        const double src[2] = {dt * (2.0 - a.omega) * 0.125 * a.b1, dt * (2.0 - a.omega) * 0.125 * a.b2};
+        R f[4][6];  // f^0 - f_rest
+        const LawP<R> m = law_cast<R>(law_at(a.m, n));
+        if (!init_node_ofs<R>(a, x, y, m, f)) atomicOr(a.status, ST_BAD_J);
+        // step-0 collision (Eqs. 10, 12, 14) on the offsets from the rest
+        // state, which the collision leaves fixed
+        R Un[6], dJ;
+        for (int k = 0; k < 6; ++k) Un[k] = (f[0][k] + f[2][k]) + (f[1][k] + f[3][k]);
+        Un[0] += (R)(0.5 * dt * a.b1);
+        Un[1] += (R)(0.5 * dt * a.b2);
+        const R Gn[4] = {Un[2], Un[3], Un[4], Un[5]};
+        R Pn[4], feq[4][6];
+        piola_any_t<R>(a.m.law, Gn, m, Pn, dJ);
+        feq_ofs<R>(Un, Pn, c, feq);
+        const R src[2] = {(R)(dt * (2.0 - a.omega) * 0.125 * a.b1), (R)(dt * (2.0 - a.omega) * 0.125 * a.b2)};
         for (int q = 0; q < 4; ++q)
             for (int k = 0; k < 6; ++k) {
-                double fs = f[q][k] + a.omega * (feq[q][k] - f[q][k]) + (k < 2 ? src[k] : 0.0);
-                if (k == 2 || k == 5) fs -= 0.25; // store the offset from f_rest
+                R fs = f[q][k] + w * (feq[q][k] - f[q][k]);
+                if (k < 2) fs += src[k];
                 fout[pidx(a.L, q, k, x, y)] = to_store<T>(fs);
             }
         for (int k = 0; k < 2; ++k) {
             const double u0 = a.u0 ? a.u0[k * N + n] : 0.0;
-            a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] = (u0 - 0.5 * dt * a.U0[k * N + n]) + dt * Un[k];
+            a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] =
+                (u0 - 0.5 * dt * a.U0[k * N + n]) + dt * (double)Un[k];
         }
     }
 }

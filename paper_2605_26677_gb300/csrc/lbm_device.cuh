@@ -329,17 +329,24 @@ __device__ __forceinline__ void jvp_inv(const R G[4], const R dF[4], const LawP<
     for (int k = 0; k < 4; ++k) dP[k] = Pd[k].d;
 }
 
+// Stress of any law chosen at run time, from G = F - I, in compute type R
+template <typename R>
+__device__ inline void piola_any_t(int law, const R G[4], const LawP<R> &m, R P[4], R &dJ)
+{
+    switch (law) {
+    case LAW_SVK: piola_ofs<LAW_SVK, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_NH: piola_ofs<LAW_NH, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_LOGNH: piola_ofs<LAW_LOGNH, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_MR: piola_ofs<LAW_MR, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    case LAW_YEOH: piola_ofs<LAW_YEOH, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    default: piola_ofs<LAW_GENT, R>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
+    }
+}
+
 // FP64 stress of any law chosen at run time, from G = F - I
 __device__ inline void piola_any(int law, const double G[4], const LawP<double> &m, double P[4], double &dJ)
 {
-    switch (law) {
-    case LAW_SVK: piola_ofs<LAW_SVK, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    case LAW_NH: piola_ofs<LAW_NH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    case LAW_LOGNH: piola_ofs<LAW_LOGNH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    case LAW_MR: piola_ofs<LAW_MR, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    case LAW_YEOH: piola_ofs<LAW_YEOH, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    default: piola_ofs<LAW_GENT, double>(G[0], G[1], G[2], G[3], m, P[0], P[1], P[2], P[3], dJ); break;
-    }
+    piola_any_t<double>(law, G, m, P, dJ);
 }
 
 // Strain energy W(F) of the same laws (diagnostics only), from G = F - I.
@@ -373,33 +380,35 @@ __device__ __forceinline__ double energy_ofs(int law, double G11, double G12, do
     return -0.5 * mu * m.p2 * log1p(-A / m.p2) + vol;
 }
 
-// Jacobian-vector product dP = C : dF of the tangent of Eq. (4) (Eq. 8), FP64.
-__device__ __forceinline__ void tangent_jvp(int law, const double F[4], const double dF[4], const LawP<double> &m,
-                                            double dP[4])
+
+// Jacobian-vector product dP = C : dF of the tangent of Eq. (4) (Eq. 8), in
+// compute type R.
+template <typename R>
+__device__ __forceinline__ void tangent_jvp_t(int law, const R F[4], const R dF[4], const LawP<R> &m, R dP[4])
 {
-    const double lam = m.lam, mu = m.mu;
+    const R lam = m.lam, mu = m.mu;
     if (law >= LAW_MR) {
-        const double G[4] = {F[0] - 1.0, F[1], F[2], F[3] - 1.0};
+        const R G[4] = {F[0] - R(1.0), F[1], F[2], F[3] - R(1.0)};
         if (law == LAW_MR)
-            jvp_inv<LAW_MR, double>(G, dF, m, dP);
+            jvp_inv<LAW_MR, R>(G, dF, m, dP);
         else if (law == LAW_YEOH)
-            jvp_inv<LAW_YEOH, double>(G, dF, m, dP);
+            jvp_inv<LAW_YEOH, R>(G, dF, m, dP);
         else
-            jvp_inv<LAW_GENT, double>(G, dF, m, dP);
+            jvp_inv<LAW_GENT, R>(G, dF, m, dP);
         return;
     }
     if (law == LAW_SVK) {
         // dP = dF S + F dS, dS = lambda tr(dE) I + 2 mu dE, dE = (dF^T F + F^T dF) / 2
-        const double E11 = 0.5 * (F[0] * F[0] + F[2] * F[2] - 1.0);
-        const double E22 = 0.5 * (F[1] * F[1] + F[3] * F[3] - 1.0);
-        const double E12 = 0.5 * (F[0] * F[1] + F[2] * F[3]);
-        const double trE = E11 + E22;
-        const double S11 = lam * trE + 2.0 * mu * E11, S22 = lam * trE + 2.0 * mu * E22, S12 = 2.0 * mu * E12;
-        const double dE11 = dF[0] * F[0] + dF[2] * F[2];
-        const double dE22 = dF[1] * F[1] + dF[3] * F[3];
-        const double dE12 = 0.5 * (dF[0] * F[1] + dF[2] * F[3] + F[0] * dF[1] + F[2] * dF[3]);
-        const double dtr = dE11 + dE22;
-        const double dS11 = lam * dtr + 2.0 * mu * dE11, dS22 = lam * dtr + 2.0 * mu * dE22, dS12 = 2.0 * mu * dE12;
+        const R E11 = R(0.5) * (F[0] * F[0] + F[2] * F[2] - R(1.0));
+        const R E22 = R(0.5) * (F[1] * F[1] + F[3] * F[3] - R(1.0));
+        const R E12 = R(0.5) * (F[0] * F[1] + F[2] * F[3]);
+        const R trE = E11 + E22;
+        const R S11 = lam * trE + R(2.0) * mu * E11, S22 = lam * trE + R(2.0) * mu * E22, S12 = R(2.0) * mu * E12;
+        const R dE11 = dF[0] * F[0] + dF[2] * F[2];
+        const R dE22 = dF[1] * F[1] + dF[3] * F[3];
+        const R dE12 = R(0.5) * (dF[0] * F[1] + dF[2] * F[3] + F[0] * dF[1] + F[2] * dF[3]);
+        const R dtr = dE11 + dE22;
+        const R dS11 = lam * dtr + R(2.0) * mu * dE11, dS22 = lam * dtr + R(2.0) * mu * dE22, dS12 = R(2.0) * mu * dE12;
         dP[0] = dF[0] * S11 + dF[1] * S12 + F[0] * dS11 + F[1] * dS12;
         dP[1] = dF[0] * S12 + dF[1] * S22 + F[0] * dS12 + F[1] * dS22;
         dP[2] = dF[2] * S11 + dF[3] * S12 + F[2] * dS11 + F[3] * dS12;
@@ -408,28 +417,36 @@ __device__ __forceinline__ void tangent_jvp(int law, const double F[4], const do
     }
     // NH:    dP = mu dF + lambda J^2 (H : dF) H + [mu - (lambda/2)(J^2 - 1)] H dF^T H
     // logNH: dP = mu dF + lambda     (H : dF) H + [mu - lambda log J]        H dF^T H
-    const double J = F[0] * F[3] - F[1] * F[2];
-    const double H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
-    const double HdF = H[0] * dF[0] + H[1] * dF[1] + H[2] * dF[2] + H[3] * dF[3];
-    double a, b;
+    const R J = F[0] * F[3] - F[1] * F[2];
+    const R H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    const R HdF = H[0] * dF[0] + H[1] * dF[1] + H[2] * dF[2] + H[3] * dF[3];
+    R a, b;
     if (law == LAW_NH) {
         a = lam * J * J;
-        b = mu - 0.5 * lam * (J * J - 1.0);
+        b = mu - R(0.5) * lam * (J * J - R(1.0));
     } else {
         a = lam;
         b = mu - lam * log(J);
     }
     // (H dF^T H)_iA = sum_{B,k} H_iB dF_kB H_kA
-    double M[4];
+    R M[4];
     for (int i = 0; i < 2; ++i)
         for (int A = 0; A < 2; ++A) {
-            double s = 0.0;
+            R s = R(0);
             for (int k = 0; k < 2; ++k)
                 for (int B = 0; B < 2; ++B) s += H[i * 2 + B] * dF[k * 2 + B] * H[k * 2 + A];
             M[i * 2 + A] = s;
         }
     for (int m = 0; m < 4; ++m) dP[m] = mu * dF[m] + a * HdF * H[m] + b * M[m];
 }
+
+// Jacobian-vector product dP = C : dF of the tangent of Eq. (4) (Eq. 8), FP64.
+__device__ __forceinline__ void tangent_jvp(int law, const double F[4], const double dF[4], const LawP<double> &m,
+                                            double dP[4])
+{
+    tangent_jvp_t<double>(law, F, dF, m, dP);
+}
+
 
 // Boundary-data time function g(t) (shapes of Eqs. 33, 35 and Sec. 5.4),
 // evaluated on the host once per step and edge.
