@@ -23,6 +23,7 @@
 // Newton solve for F^b, which depends on the boundary node's tangential
 // column and mu, evaluated at the F^b the forward stored in the ghost cell;
 // periodic: h_d goes back to the node it was copied from).
+#include "lbm_launch.cuh"
 #include "lbm_init_core.cuh"
 #include "lbm_step_core.cuh"
 
@@ -89,6 +90,7 @@ __device__ __forceinline__ void traction_ift(int e, const T Gb[4], const T hd[6]
 template <typename S, int LAW, int VEC>
 __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjArgs<typename Prec<S>::R> a)
 {
+    pdl_enter();
     using T = typename Prec<S>::R;
     using PK = Pack<S, VEC>;
     using PT = Pack<T, VEC>;
@@ -555,11 +557,10 @@ static cudaError_t launch_adj_s(int law, const void *args, int grid, cudaStream_
     constexpr int VEC = adj_vec<S>();
     const auto &a = *static_cast<const AdjArgs<T> *>(args);
     switch (law) {
-    case LAW_SVK: k_adj<S, LAW_SVK, VEC><<<grid, 128, 0, st>>>(a); break;
-    case LAW_NH: k_adj<S, LAW_NH, VEC><<<grid, 128, 0, st>>>(a); break;
-    default: k_adj<S, LAW_LOGNH, VEC><<<grid, 128, 0, st>>>(a); break;
+    case LAW_SVK: return launch_pdl(k_adj<S, LAW_SVK, VEC>, grid, 128, 0, st, a);
+    case LAW_NH: return launch_pdl(k_adj<S, LAW_NH, VEC>, grid, 128, 0, st, a);
+    default: return launch_pdl(k_adj<S, LAW_LOGNH, VEC>, grid, 128, 0, st, a);
     }
-    return cudaGetLastError();
 }
 
 int adj_vec_for(int storage) { return storage == STORE_F64 ? adj_vec<double>() : adj_vec<float>(); }

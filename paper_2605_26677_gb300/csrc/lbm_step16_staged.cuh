@@ -5,6 +5,7 @@
 #include "lbm_internal.h"
 #include "lbm_step_core.cuh"
 #include "lbm_bulk.cuh"
+#include "lbm_launch.cuh"
 #include <cstdlib>
 #include <cstring>
 
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const 
     using WV = Words<W>;
     using PD = Pack<double, 4>;
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_enter();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gw = blockIdx.x * G::WARPS + wid, nw = gridDim.x * G::WARPS;
     const int nx = a.L.nx, ny = a.L.ny;
@@ -246,8 +248,7 @@ static cudaError_t launch_step16s(const StepArgs<float> &a, int grid, cudaStream
 {
     const cudaError_t e = step16s_prepare<S, LAW, NS, FUSE>();
     if (e != cudaSuccess) return e;
-    k_step16s<S, LAW, NS, FUSE><<<grid, 128, Stage16<NS>::SMEM, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_step16s<S, LAW, NS, FUSE>, grid, 128, (size_t)Stage16<NS>::SMEM, st, a);
 }
 
 // Launches the staged kernel when it is the selected one (true, status in

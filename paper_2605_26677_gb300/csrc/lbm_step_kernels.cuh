@@ -6,11 +6,13 @@
 #include "lbm_internal.h"
 #include "lbm_step_core.cuh"
 #include "lbm_step16_staged.cuh"
+#include "lbm_launch.cuh"
 
 namespace tlv {
 template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -24,6 +26,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
 template <typename S, int LAW, int V, bool FUSE>
 __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -89,33 +92,25 @@ __global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
 template <typename S, int LAW>
 static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
 {
+    constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors (unpacked kernels)
     if (a.mufield) {
         // per-node material: FP64 and FP32 storage, SVK / NH / log-NH
         if constexpr (sizeof(S) == 2 || LAW > LAW_LOGNH) {
             return cudaErrorNotSupported;
         } else {
-            if (fuse)
-                k_step<S, LAW, 16 / sizeof(S), true, true><<<grid, 128, 0, st>>>(a);
-            else
-                k_step<S, LAW, 16 / sizeof(S), false, true><<<grid, 128, 0, st>>>(a);
-            return cudaGetLastError();
+            return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true>, grid, 128, 0, st, a)
+                        : launch_pdl(k_step<S, LAW, VEC, false, true>, grid, 128, 0, st, a);
         }
     }
     if constexpr (sizeof(S) == 2) {
         cudaError_t e;
         if (launch_step16_staged<S, LAW>(a, fuse, grid, st, e)) return e;
-        if (fuse)
-            k_step16<S, LAW, STEP16_V, true><<<grid, 128, 0, st>>>(a);
-        else
-            k_step16<S, LAW, STEP16_V, false><<<grid, 128, 0, st>>>(a);
+        return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true>, grid, 128, 0, st, a)
+                    : launch_pdl(k_step16<S, LAW, STEP16_V, false>, grid, 128, 0, st, a);
     } else {
-        constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors
-        if (fuse)
-            k_step<S, LAW, VEC, true><<<grid, 128, 0, st>>>(a);
-        else
-            k_step<S, LAW, VEC, false><<<grid, 128, 0, st>>>(a);
+        return fuse ? launch_pdl(k_step<S, LAW, VEC, true>, grid, 128, 0, st, a)
+                    : launch_pdl(k_step<S, LAW, VEC, false>, grid, 128, 0, st, a);
     }
-    return cudaGetLastError();
 }
 
 template <typename S>
