@@ -36,7 +36,11 @@
  *     converge, a non-finite state) are latched in a device status word; the
  *     next call that synchronises (lbm_step, lbm_sync, lbm_read_*) returns the
  *     matching LBM_ERR_* code. The state stays readable after such an error.
- *     lbm_init clears the latch.
+ *     lbm_init clears the latch. The staged 16-bit step kernel (selected by
+ *     LBM_STEP16=staged in the environment) bounds each wait for its
+ *     asynchronous copies to one second; one that runs out is latched the
+ *     same way and returned as LBM_ERR_CUDA, and the steps that followed it
+ *     are not valid.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -57,7 +61,8 @@ typedef enum {
     LBM_ERR_ARG = 1,            /* an argument is out of range or inconsistent        */
     LBM_ERR_STATE = 2,          /* call out of order (e.g. step before init)          */
     LBM_ERR_OOM = 3,            /* device or host allocation failed                   */
-    LBM_ERR_CUDA = 4,           /* a CUDA runtime call failed                         */
+    LBM_ERR_CUDA = 4,           /* a CUDA runtime call failed, or a bounded device    *
+                                 * wait for asynchronous copies ran out               */
     LBM_ERR_NONPOSITIVE_J = 5,  /* some node reached J = det F <= 0 (Sec. 2.2)        */
     LBM_ERR_NEWTON = 6,         /* a traction-edge Newton solve failed (Sec. 3.6.2)   */
     LBM_ERR_NONFINITE = 7,      /* the state became NaN or infinite                   */
