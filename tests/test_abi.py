@@ -43,7 +43,10 @@ def test_library_links_no_torch(lbm):
     import subprocess
 
     out = subprocess.run(["ldd", lbm.LIB_PATH], capture_output=True, text=True).stdout
-    assert "torch" not in out and "c10" not in out
+    # library names only: the load addresses ldd prints are random hex and
+    # may contain "c10"
+    names = [ln.split()[0] for ln in out.splitlines() if ln.strip()]
+    assert names and not [n for n in names if re.match(r"lib(torch|c10)", os.path.basename(n))], out
 
 
 @pytest.mark.parametrize("kw,err", [
