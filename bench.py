@@ -197,6 +197,25 @@ def timed_steps(lbm, torch, L, steps, warmup, dist, census_steps=10):
     return ms, info
 
 
+def recorded_fp64_counts():
+    """FP64 instructions per node-update of the FP64 step kernel (committed
+    ncu record) and the FP64 instruction rate of the GPU derived from its
+    nominal FP64 rate, or None when the kernel source changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "fp64_step_kernel_counts.txt")
+    try:
+        kv = dict(ln.split("=", 1) for ln in open(path).read().split() if "=" in ln)
+        h = hashlib.sha256()
+        for f in ("lbm_step_kernels.cuh", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_edges.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2605_26677_gb300", "csrc", f), "rb").read())
+        if kv.get("source_sha256") != h.hexdigest():
+            return None
+        return float(kv["fp64_inst_per_node"]), float(kv["fp64_inst_peak_per_s"])
+    except Exception:
+        return None
+
+
 def recorded_traffic():
     """DRAM bytes per bulk-kernel launch from the committed ncu summary, or
     None when the kernel source changed since the capture."""
@@ -285,6 +304,14 @@ def run_ours(args, rank, ws, dist):
             "value": N * k / (ms64 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
             "kernel_GBs": b64 * N / (i64["step_kernel_ms"] * 1e-3) / 1e9, "bytes_per_node": b64,
             "note": "FP64 populations (parity mode); FP64 ALU-bound on GB300"}
+        fp64 = recorded_fp64_counts()
+        if fp64 is not None:
+            ach = fp64[0] * N / (i64["step_kernel_ms"] * 1e-3)
+            forms["fp64_clamped_specimen_4096x2048"]["roofline"] = {
+                "bound": "alu", "achieved": ach, "peak": fp64[1], "unit": "FP64 inst/s", "frac": ach / fp64[1],
+                "fp64_inst_per_node": fp64[0],
+                "peak_source": "derived: nominal 1.25 TFLOP/s FP64 = 2 FMA per SM per clock x 152 SMs x 2070 MHz; "
+                               "every FP64 instruction (FMA, add, multiply) occupies the FP64 pipe alike"}
         for name, st in (("bf16", lbm.LBM_STORE_BF16), ("f16", lbm.LBM_STORE_F16)):
             L = setup_ctx(lbm, w, st, U0, u0)
             msh, ih = timed_steps(lbm, torch, L, k, 5, None)
@@ -327,6 +354,7 @@ def run_ours(args, rank, ws, dist):
                    "l2": "inputs larger than L2 (%.2f GB moved per step)" % (bpn * N / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                      "traffic": None if traffic_bpn is None else traffic_bpn * N,
                      "kernel": "k_step (fused pull-stream + collide + quadrature)",
                      "bytes_per_node_update": bpn, "launch_ms": kern_ms,
