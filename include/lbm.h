@@ -66,7 +66,7 @@ typedef enum {
     LBM_ERR_NONPOSITIVE_J = 5,  /* some node reached J = det F <= 0 (Sec. 2.2)        */
     LBM_ERR_NEWTON = 6,         /* a traction-edge Newton solve failed (Sec. 3.6.2)   */
     LBM_ERR_NONFINITE = 7,      /* the state became NaN or infinite                   */
-    LBM_ERR_UNSUPPORTED = 8     /* valid request this build does not implement        */
+    LBM_ERR_UNSUPPORTED = 8     /* valid request the library does not implement       */
 } lbm_status;
 
 /* Storage of the populations. Compute is in the storage precision (F64, F32).
