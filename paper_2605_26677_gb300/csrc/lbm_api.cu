@@ -146,6 +146,7 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
         a.profile[e] = c->edge[e].profile;
     }
     a.gdev = nullptr;
+    a.k16 = c->k16;
     return a;
 }
 
@@ -693,6 +694,61 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     return LBM_OK;
 }
 
+// The two 16-bit step kernels (registers; rows staged in shared memory)
+// produce bit-identical states, and which is faster depends on the lattice:
+// time both on this one and keep the faster. The trials read the current
+// buffer, whose ghost cells are refreshed first exactly as the first step
+// would, and write only the other buffer, which the first real step
+// overwrites; u* and the status word go to scratch, so the state is untouched.
+// Skipped when LBM_STEP16 forces a kernel, for the extrapolated F^b form, or
+// when the scratch cannot be allocated (the register kernel then runs).
+static lbm_status tune_step16(lbm_ctx *c)
+{
+    if (c->eb != 2 || c->cfg.fb_mode != LBM_FB_NODE || tlv::step16_env_choice() >= 0) return LBM_OK;
+    if (c->ghosts_dirty) {
+        lbm_status s = refresh_ghosts<float>(c);
+        if (s != LBM_OK) return s;
+    }
+    double *us = nullptr;
+    int *st = nullptr;
+    const size_t ubytes = (size_t)2 * c->L.uplane * sizeof(double);
+    if (cudaMallocAsync((void **)&us, ubytes, c->st) != cudaSuccess) {
+        cudaGetLastError();  // clear it: without scratch the register kernel runs
+        return LBM_OK;
+    }
+    if (cudaMallocAsync((void **)&st, sizeof(int), c->st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(us, c->st);
+        return LBM_OK;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaMemsetAsync(us, 0, ubytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), c->st);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    StepArgs<float> a = step_args<float>(c, c->cur);
+    a.ustar = us;
+    a.status = st;
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        a.k16 = v;
+        e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+            e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
+    }
+    if (e == cudaSuccess) c->k16 = ms[1] < ms[0] ? 1 : 0;
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFreeAsync(us, c->st);
+    cudaFreeAsync(st, c->st);
+    CK(c, e);
+    return LBM_OK;
+}
+
 static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
@@ -730,6 +786,8 @@ lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t orde
     if (du) cudaFreeAsync(du, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "copying the initial state");
     if (s != LBM_OK) return s;
+    s = tune_step16(c);
+    if (s != LBM_OK) return s;
     return sync_status(c);
 }
 
@@ -739,7 +797,8 @@ lbm_status lbm_init_device(lbm_ctx *c, const double *U0_dev, const double *u0_de
     lbm_status s = init_checks(c, U0_dev, order);
     if (s != LBM_OK) return s;
     CK(c, cudaSetDevice(c->cfg.device));
-    return init_common(c, U0_dev, u0_dev, order);
+    s = init_common(c, U0_dev, u0_dev, order);
+    return s != LBM_OK ? s : tune_step16(c);
 }
 
 lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)

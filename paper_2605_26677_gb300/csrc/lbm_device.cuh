@@ -158,6 +158,8 @@ struct StepArgs {
     double value[4][2], g[4];
     const double *gdev;          // if set, the time factors are read here instead of g
     const double *profile[4];
+    int k16;                     // 16-bit storage: step kernel chosen for the context (0 register,
+                                 // 1 staged); read by the host launcher only
 };
 
 // A batch of lattices for one persistent launch

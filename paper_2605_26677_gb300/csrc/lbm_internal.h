@@ -1,6 +1,8 @@
 // lbm_internal.h -- host-side declarations shared by the library's
 // translation units (kernel launchers); not part of the public C ABI.
 #pragma once
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -9,6 +11,22 @@
 
 #include "lbm.h"
 #include "lbm_device.cuh"
+
+namespace tlv {
+// 16-bit step kernel forced by the environment: LBM_STEP16=regs (register
+// kernel, 0) or LBM_STEP16=staged (shared-memory staged kernel, 1); -1 when
+// unset, and each context then uses the one lbm_init timed faster.
+inline int step16_env_choice()
+{
+    static const int k = [] {
+        const char *v = std::getenv("LBM_STEP16");
+        if (v && !std::strcmp(v, "regs")) return 0;
+        if (v && !std::strcmp(v, "staged")) return 1;
+        return -1;
+    }();
+    return k;
+}
+} // namespace tlv
 
 // One lattice: the object behind the opaque lbm_ctx handle of the C ABI.
 struct lbm_ctx {
@@ -38,6 +56,7 @@ struct lbm_ctx {
     std::vector<double> tab_t[4], tab_g[4];  // per-edge tabulated g(t) (LBM_T_TABLE)
     double *d_mufield = nullptr;  // per-node mu, compact FP64 (N), or nullptr
     void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
+    int k16 = 0;                  // 16-bit storage: step kernel (0 register, 1 staged), timed at init
 };
 
 

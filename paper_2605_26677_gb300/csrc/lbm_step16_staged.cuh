@@ -211,19 +211,16 @@ __global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const 
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
 
-// Which 16-bit step kernel runs: the register kernel (default: faster or
-// equal on every lattice measured but one; BF16 us per step, register /
-// staged: 2896^2 periodic 187.0 / 194.4, 6144 x 2048 clamped 273.9 / 281.5,
-// 8192^2 periodic 1391.5 / 1591.8, 4096 x 2048 clamped 192.3 / 185.0) or
-// the staged kernel ("LBM_STEP16=staged" in the environment). Read once per
-// process.
-static int step16_stages()
+// Which 16-bit step kernel runs: LBM_STEP16 in the environment when set
+// (step16_env_choice), else the context's own choice (StepArgs::k16), which
+// lbm_init makes by timing both on the lattice. The register kernel is the
+// faster one on most lattices measured (BF16 us per step, register / staged:
+// 2896^2 periodic 187.0 / 194.4, 8192^2 periodic 1391.5 / 1591.8), the staged
+// one on some (4096 x 2048 clamped 192.3 / 185.0).
+static int step16_stages(int ctx_choice)
 {
-    static const int ns = [] {
-        const char *v = std::getenv("LBM_STEP16");
-        return (v && !std::strcmp(v, "staged")) ? 1 : 0;
-    }();
-    return ns;
+    const int e = step16_env_choice();
+    return (e >= 0 ? e : ctx_choice) == 1 ? 1 : 0;
 }
 
 // The staged kernel's dynamic shared memory exceeds the 48 KB default: raise
@@ -256,20 +253,20 @@ static cudaError_t launch_step16s(const StepArgs<float> &a, int grid, cudaStream
 template <typename S, int LAW>
 static bool launch_step16_staged(const StepArgs<float> &a, bool fuse, int grid, cudaStream_t st, cudaError_t &err)
 {
-    if (step16_stages() != 1) return false;
+    if (step16_stages(a.k16) != 1) return false;
     err = fuse ? launch_step16s<S, LAW, 1, true>(a, grid, st) : launch_step16s<S, LAW, 1, false>(a, grid, st);
     return true;
 }
 
-// Resident blocks per SM of the selected staged kernel (fused form) in n,
-// status in err; false when the register kernel is selected.
+// Resident blocks per SM of the staged kernel (fused form) in n, status in
+// err. The grid is sized once for both 16-bit kernels, which either may run.
 template <typename S, int LAW>
-static bool step16_staged_blocks(int &n, cudaError_t &err)
+static cudaError_t step16_staged_blocks(int &n)
 {
-    if (step16_stages() != 1) return false;
-    if ((err = step16s_prepare<S, LAW, 1, true>()) == cudaSuccess)
+    cudaError_t err = step16s_prepare<S, LAW, 1, true>();
+    if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step16s<S, LAW, 1, true>, 128, Stage16<1>::SMEM);
-    return true;
+    return err;
 }
 
 } // namespace tlv

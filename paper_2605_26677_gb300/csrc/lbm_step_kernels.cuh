@@ -148,8 +148,10 @@ static int step_blocks_t()
     int n = 0;
     cudaError_t e = cudaSuccess;
     if constexpr (sizeof(S) == 2) {
-        if (!step16_staged_blocks<S, LAW>(n, e))
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step16<S, LAW, STEP16_V, true>, 128, 0);
+        int ns = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step16<S, LAW, STEP16_V, true>, 128, 0);
+        if (e == cudaSuccess) e = step16_staged_blocks<S, LAW>(ns);
+        if (e == cudaSuccess && ns < n) n = ns;
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, LAW, 16 / sizeof(S), true>, 128, 0);
     }

@@ -1,11 +1,13 @@
-"""The 16-bit step kernels against each other: the register kernel (the
-default) and the staged kernel (rows moved into shared memory by bulk
-asynchronous copies; LBM_STEP16=staged in the environment) run the same
+"""The 16-bit step kernels against each other: the register kernel
+(LBM_STEP16=regs in the environment) and the staged kernel (rows moved into
+shared memory by bulk asynchronous copies; LBM_STEP16=staged) run the same
 tasks through the same per-node arithmetic, so after any number of steps
-their states, displacements and diagnostics agree bit for bit. The kernel is
-chosen once per process, so each one runs in a child process over the same
-cases; their agreement with the oracle is the 16-bit part of
-test_gpu_parity, which runs the default kernel.
+their states, displacements and diagnostics agree bit for bit; so does the
+default, where lbm_init times both kernels on the lattice with trial steps
+that must leave the state untouched, and keeps the faster. The choice is
+read once per process, so each variant runs in a child process over the
+same cases; agreement with the oracle is the 16-bit part of
+test_gpu_parity, which runs the default.
 
 Cases: ragged widths (1000 = 7 segments of 128 and a tail of 104; 131 = one
 segment and a tail of 3), every edge rule with the fused ghost writes, the
@@ -72,10 +74,11 @@ def built():
 
 
 def test_staged_and_register_kernels_bit_identical(tmp_path):
-    ref = run_variant(tmp_path, None)
-    got = run_variant(tmp_path, "staged")
-    assert set(got) == set(ref)
-    for k in ref:
-        assert np.all(np.isfinite(ref[k])), k
-        same = np.array_equal(got[k].view(np.uint64), ref[k].view(np.uint64))
-        assert same, (k, float(np.max(np.abs(got[k] - ref[k]))))
+    ref = run_variant(tmp_path, "regs")
+    for variant in ("staged", None):
+        got = run_variant(tmp_path, variant)
+        assert set(got) == set(ref)
+        for k in ref:
+            assert np.all(np.isfinite(ref[k])), k
+            same = np.array_equal(got[k].view(np.uint64), ref[k].view(np.uint64))
+            assert same, (variant, k, float(np.max(np.abs(got[k] - ref[k]))))
