@@ -187,12 +187,7 @@ lbm_status lbm_set_boundary_table(lbm_ctx *ctx, int32_t edge, int32_t n, const d
  * stencils next to non-periodic edges) for the gradients. Sets t = 0, clears
  * the status latch and starts u* = u0 - (dt/2) v0. Requires lbm_set_material;
  * checks edge pairing and c > sqrt(lambda + 2 mu) (the rest-state P-wave
- * speed). Synchronises. With BF16 or FP16 storage (and the node form of F^b)
- * it also times the library's two 16-bit step kernels, which give identical
- * results, with a few trial steps that leave the state untouched, and keeps
- * the faster for this context; the trials take a u*-sized scratch
- * allocation for their duration. LBM_STEP16=regs or LBM_STEP16=staged in
- * the environment skips the trials and forces that kernel. */
+ * speed). Synchronises. */
 lbm_status lbm_init(lbm_ctx *ctx, const double *U0, const double *u0, int32_t order);
 
 /* As lbm_init with device pointers (6N and 2N float64, NULL u0 = 0); enqueued
@@ -200,7 +195,14 @@ lbm_status lbm_init(lbm_ctx *ctx, const double *U0, const double *u0, int32_t or
 lbm_status lbm_init_device(lbm_ctx *ctx, const double *U0_dev, const double *u0_dev, int32_t order);
 
 /* Advance nsteps >= 0 time steps (Sec. 3.7), then wait and return the
- * latched device status. */
+ * latched device status. With BF16 or FP16 storage (and the node form of
+ * F^b) the first call with nsteps > 0 after lbm_init or lbm_init_device
+ * first times the library's two 16-bit step kernels, which give identical
+ * results, with a few trial steps that leave the state untouched, and keeps
+ * the faster for this context (the trials take a u*-sized scratch
+ * allocation while they run). Until then, and for lbm_step_async, the
+ * register kernel runs. LBM_STEP16=regs or LBM_STEP16=staged in the
+ * environment skips the trials and forces that kernel. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* As lbm_step without waiting; check later with lbm_sync. */

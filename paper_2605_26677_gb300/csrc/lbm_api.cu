@@ -691,12 +691,14 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     c->step = 0;
     c->initialized = true;
     c->ghosts_dirty = true;
+    c->k16_pending = true;
     return LBM_OK;
 }
 
 // The two 16-bit step kernels (registers; rows staged in shared memory)
 // produce bit-identical states, and which is faster depends on the lattice:
-// time both on this one and keep the faster. The trials read the current
+// the first lbm_step after an initialization times both on this one and
+// keeps the faster. The trials read the current
 // buffer, whose ghost cells are refreshed first exactly as the first step
 // would, and write only the other buffer, which the first real step
 // overwrites; u* and the status word go to scratch, so the state is untouched.
@@ -786,8 +788,6 @@ lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t orde
     if (du) cudaFreeAsync(du, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "copying the initial state");
     if (s != LBM_OK) return s;
-    s = tune_step16(c);
-    if (s != LBM_OK) return s;
     return sync_status(c);
 }
 
@@ -797,8 +797,7 @@ lbm_status lbm_init_device(lbm_ctx *c, const double *U0_dev, const double *u0_de
     lbm_status s = init_checks(c, U0_dev, order);
     if (s != LBM_OK) return s;
     CK(c, cudaSetDevice(c->cfg.device));
-    s = init_common(c, U0_dev, u0_dev, order);
-    return s != LBM_OK ? s : tune_step16(c);
+    return init_common(c, U0_dev, u0_dev, order);
 }
 
 lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
@@ -814,6 +813,14 @@ lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
 
 lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
 {
+    if (c && c->initialized && c->k16_pending && nsteps > 0) {
+        // the first synchronising step after an initialization picks the
+        // 16-bit step kernel for the lattice
+        lbm_status s = check_edges(c);
+        if (s == LBM_OK) s = tune_step16(c);
+        if (s != LBM_OK) return s;
+        c->k16_pending = false;
+    }
     lbm_status s = lbm_step_async(c, nsteps);
     if (s != LBM_OK) return s;
     return sync_status(c);

@@ -56,7 +56,8 @@ struct lbm_ctx {
     std::vector<double> tab_t[4], tab_g[4];  // per-edge tabulated g(t) (LBM_T_TABLE)
     double *d_mufield = nullptr;  // per-node mu, compact FP64 (N), or nullptr
     void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
-    int k16 = 0;                  // 16-bit storage: step kernel (0 register, 1 staged), timed at init
+    int k16 = 0;                  // 16-bit storage: step kernel (0 register, 1 staged)
+    bool k16_pending = false;     // the next lbm_step times both 16-bit kernels first
 };
 
 
