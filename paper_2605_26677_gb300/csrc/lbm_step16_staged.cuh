@@ -50,8 +50,11 @@ struct Stage16 {
                   "16-byte copy destinations, 32-byte u* vectors");
 };
 
+// inject_stall != 0 (a test of the bounded wait, see stall_test_once): the
+// first task of warp 0 expects 16 bytes more than its copies deliver, so its
+// stage never completes and the wait runs out.
 template <typename S, int LAW, int NS, bool FUSE>
-__global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const StepArgs<float> a)
+__global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const StepArgs<float> a, int inject_stall)
 {
     using G = Stage16<NS>;
     constexpr int V = 4, W = 2, SW = G::SW;
@@ -81,7 +84,8 @@ __global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const 
         const unsigned rem = (unsigned)min(SW, nx - x0s);
         const unsigned n1 = (rem + 7) & ~7u, n0 = G::HALO + n1, n2 = (rem + 8) & ~7u, nu = (rem + 1) & ~1u;
         uint64_t *b = bar + s;
-        mbar_expect(b, 12u * (n0 + n2 + 2u * n1) + 16u * nu);
+        const unsigned phantom = (inject_stall && task == gw && gw == 0) ? 16u : 0u;
+        mbar_expect(b, 12u * (n0 + n2 + 2u * n1) + 16u * nu + phantom);
         const long long row = (long long)(y + 1) * pitch + a.L.xoff + x0s;
         unsigned short *d = reinterpret_cast<unsigned short *>(stages + s * G::BYTES);
 #pragma unroll 1
@@ -240,12 +244,26 @@ static cudaError_t step16s_prepare()
     return e;
 }
 
+// Test of the staged kernel's bounded wait: with LBM_STEP16_STALL_TEST=1 in
+// the environment, the first staged launch of the process makes one warp's
+// wait run out (about two seconds; the step then reports LBM_ERR_CUDA and its
+// result is not valid). Every later launch runs normally.
+static int stall_test_once()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("LBM_STEP16_STALL_TEST");
+        return v && !std::strcmp(v, "1");
+    }();
+    static int used = 0;
+    return on && __atomic_exchange_n(&used, 1, __ATOMIC_ACQ_REL) == 0 ? 1 : 0;
+}
+
 template <typename S, int LAW, int NS, bool FUSE>
 static cudaError_t launch_step16s(const StepArgs<float> &a, int grid, cudaStream_t st)
 {
     const cudaError_t e = step16s_prepare<S, LAW, NS, FUSE>();
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_step16s<S, LAW, NS, FUSE>, grid, 128, (size_t)Stage16<NS>::SMEM, st, a);
+    return launch_pdl(k_step16s<S, LAW, NS, FUSE>, grid, 128, (size_t)Stage16<NS>::SMEM, st, a, stall_test_once());
 }
 
 // Launches the staged kernel when it is the selected one (true, status in
