@@ -731,17 +731,25 @@ static lbm_status tune_step16(lbm_ctx *c)
     StepArgs<float> a = step_args<float>(c, c->cur);
     a.ustar = us;
     a.status = st;
+    // two warm-up steps, then three rounds of three steps of each kernel,
+    // interleaved so that clock changes weigh on both alike
     float ms[2] = {0.f, 0.f};
     for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
         a.k16 = v;
-        e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->st);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-            e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
+        e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
     }
+    for (int round = 0; round < 3 && e == cudaSuccess; ++round)
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            a.k16 = v;
+            float t = 0.f;
+            e = cudaEventRecord(ev[0], c->st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+            ms[v] += t;
+        }
     if (e == cudaSuccess) c->k16 = ms[1] < ms[0] ? 1 : 0;
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
