@@ -149,8 +149,8 @@ lbm_status lbm_set_material(lbm_ctx *ctx, int32_t law, const double *params, int
 /* Per-node material (the paper's closures are pointwise, so Eq. (14) takes
  * them node by node): shear modulus mu (host, N values, finite and > 0) and
  * lambda = lam_ratio * mu, for the SVK, NH or LOGNH closure. Replaces any
- * uniform material (lbm_set_material replaces the field). FP64 and FP32
- * storage only (LBM_ERR_UNSUPPORTED otherwise). Set before lbm_init (the
+ * uniform material (lbm_set_material replaces the field). Every storage
+ * type (BF16 and FP16 step with the register kernel). Set before lbm_init (the
  * lattice-speed check of lbm_init uses the stiffest node); set later, it
  * applies from the next step on. Copied; waits for the upload. Contexts with
  * a field cannot join a batch. */

@@ -531,8 +531,6 @@ static lbm_status field_checks(lbm_ctx *c, int32_t law, const void *mu, double l
     if (!c) return fail(nullptr, LBM_ERR_ARG, "null context");
     if (law != LBM_LAW_SVK && law != LBM_LAW_NH && law != LBM_LAW_LOGNH)
         return fail(c, LBM_ERR_ARG, "material fields take the SVK, NH or LOGNH closure");
-    if (c->cfg.storage != LBM_STORE_F64 && c->cfg.storage != LBM_STORE_F32)
-        return fail(c, LBM_ERR_UNSUPPORTED, "material fields need FP64 or FP32 storage");
     if (!mu) return fail(c, LBM_ERR_ARG, "mu is NULL");
     if (!is_finite(lam_ratio) || !(lam_ratio + 2.0 > 0.0)) return fail(c, LBM_ERR_ARG, "lam_ratio must be finite and > -2");
     return LBM_OK;
@@ -702,11 +700,12 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
 // buffer, whose ghost cells are refreshed first exactly as the first step
 // would, and write only the other buffer, which the first real step
 // overwrites; u* and the status word go to scratch, so the state is untouched.
-// Skipped when LBM_STEP16 forces a kernel, for the extrapolated F^b form, or
-// when the scratch cannot be allocated (the register kernel then runs).
+// Skipped when LBM_STEP16 forces a kernel, for the extrapolated F^b form,
+// with a material field (the register kernel carries it), or when the
+// scratch cannot be allocated (the register kernel then runs).
 static lbm_status tune_step16(lbm_ctx *c)
 {
-    if (c->eb != 2 || c->cfg.fb_mode != LBM_FB_NODE || tlv::step16_env_choice() >= 0) return LBM_OK;
+    if (c->eb != 2 || c->cfg.fb_mode != LBM_FB_NODE || c->d_muplane || tlv::step16_env_choice() >= 0) return LBM_OK;
     if (c->ghosts_dirty) {
         lbm_status s = refresh_ghosts<float>(c);
         if (s != LBM_OK) return s;

@@ -314,7 +314,7 @@ struct Words {
     unsigned w[W];
 };
 
-template <typename S, int LAW, int V, bool FUSE>
+template <typename S, int LAW, int V, bool FUSE, bool MATF = false>
 __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, int lane, unsigned &flags)
 {
     constexpr int W = V / 2;  // 32-bit words per vector
@@ -389,6 +389,16 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
         // u* is read together with the populations so that its latency
         // overlaps theirs instead of following the collision
         const long long urow = (long long)y * a.L.upitch + x0;
+        // per-node mu (material field, compute-type plane in the u* layout);
+        // read only by the MATF kernels
+        float muv[V];
+        if (MATF && act)
+#pragma unroll
+            for (int h = 0; h < V / 4; ++h) {
+                const Pack<float, 4> m = *reinterpret_cast<const Pack<float, 4> *>(a.mufield + urow + 4 * h);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) muv[4 * h + e] = m.v[e];
+            }
         PD u[2][V / 4];
         if (act)
 #pragma unroll
@@ -404,7 +414,7 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) fq[q][k] = unpack16(w[q][k].w[e >> 1], e & 1, S());
-            collide_node<LAW, float>(fq, a, LawP<float>{a.lam, a.mu, a.p2, a.p3}, x0 + e < nx, flags, vel[0][e],
+            collide_node<LAW, float>(fq, a, MATF ? LawP<float>{a.lam_ratio * muv[e], muv[e], a.p2, a.p3} : LawP<float>{a.lam, a.mu, a.p2, a.p3}, x0 + e < nx, flags, vel[0][e],
                                      vel[1][e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -441,7 +451,7 @@ __device__ __forceinline__ void step16_task(const StepArgs<float> &a, int task, 
                     for (int e = 0; e < 4; ++e) u[c][h].v[e] += a.dt * (double)vel[c][4 * h + e];
                     *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow + 4 * h) = u[c][h];
                 }
-            if (FUSE) lane_ghosts<LAW, S, V>(a, reinterpret_cast<S *>(fout), row, x0, y, flags);
+            if (FUSE) lane_ghosts<LAW, S, V, MATF>(a, reinterpret_cast<S *>(fout), row, x0, y, flags);
         }
     }
 }

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
 
-template <typename S, int LAW, int V, bool FUSE>
+template <typename S, int LAW, int V, bool FUSE, bool MATF = false>
 __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
 {
     pdl_enter();
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * V - 1) / (32 * V));
     unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE>(a, task, lane, flags);
+    for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
@@ -94,9 +94,12 @@ static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fu
 {
     constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors (unpacked kernels)
     if (a.mufield) {
-        // per-node material: FP64 and FP32 storage, SVK / NH / log-NH
-        if constexpr (sizeof(S) == 2 || LAW > LAW_LOGNH) {
+        // per-node material: SVK / NH / log-NH; the 16-bit formats on the register kernel
+        if constexpr (LAW > LAW_LOGNH) {
             return cudaErrorNotSupported;
+        } else if constexpr (sizeof(S) == 2) {
+            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, true>, grid, 128, 0, st, a)
+                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, true>, grid, 128, 0, st, a);
         } else {
             return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true>, grid, 128, 0, st, a)
                         : launch_pdl(k_step<S, LAW, VEC, false, true>, grid, 128, 0, st, a);
