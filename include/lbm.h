@@ -354,7 +354,10 @@ lbm_status lbm_batch_info(const lbm_batch *b, int64_t *nodes, int32_t *launches_
  * The forward pass stores the state every checkpoint_every steps (0 = the
  * ceiling of sqrt(nsteps)); the backward pass recomputes each segment from
  * its checkpoint. Device memory: (number of checkpoints + checkpoint_every
- * - 1 + 2) population buffers. Needs FP64 or FP32 storage and the node form
+ * - 1 + 2) population buffers, and when the device has room another
+ * checkpoint_every - 1, with which the recomputation of the next segment
+ * runs on a second stream while the adjoint steps of the current one run
+ * (the gradient is the same bit for bit). Needs FP64 or FP32 storage and the node form
  * of F^b (LBM_ERR_UNSUPPORTED otherwise) and a material field
  * (LBM_ERR_STATE). The object drives the context it was created on; the
  * context must outlive it. */

@@ -30,6 +30,13 @@ struct lbm_adjoint {
     size_t fbytes = 0;
     std::vector<void *> ck;    // checkpoints f*^{kK}
     std::vector<void *> slot;  // recomputed states of one segment
+    // A second slot set and a side stream let the recomputation of segment
+    // k - 1 run while the adjoint steps of segment k do; empty when the
+    // memory for it was not available (the backward then runs serially).
+    std::vector<void *> slot2;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr};  // slot set s holds its segment
+    cudaEvent_t freed[2] = {nullptr, nullptr};  // the adjoint steps reading set s are done
     void *A[2] = {nullptr, nullptr};
     void *tug[2] = {nullptr, nullptr};  // traction-edge cotangent of G, compute type, 4 planes (u* layout)
     void *ubar = nullptr;      // compute type, 2 planes (u* layout)
@@ -141,8 +148,9 @@ lbm_status inject(lbm_adjoint *a, void *aout, int k)
     return LBM_OK;
 }
 
-// one forward step from buffer fin (state n) into fout, u* and status into scratch
-lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long n)
+// one forward step from buffer fin (state n) into fout, u* and status into
+// scratch, on stream st
+lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long n, cudaStream_t st)
 {
     lbm_ctx *c = a->c;
     if (fp64(a)) {
@@ -152,7 +160,7 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         s.ustar = a->ustar_scr;
         s.status = a->status_scr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
-        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
     } else {
         StepArgs<float> s = ctx_step_args<float>(c, c->cur);
         s.fin = fin;
@@ -160,7 +168,7 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         s.ustar = a->ustar_scr;
         s.status = a->status_scr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
-        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
     }
     return LBM_OK;
 }
@@ -182,8 +190,17 @@ void free_all(lbm_adjoint *a)
 {
     for (void *p : a->ck) cudaFree(p);
     for (void *p : a->slot) cudaFree(p);
+    for (void *p : a->slot2) cudaFree(p);
     a->ck.clear();
     a->slot.clear();
+    a->slot2.clear();
+    for (int i = 0; i < 2; ++i) {
+        if (a->ready[i]) cudaEventDestroy(a->ready[i]);
+        if (a->freed[i]) cudaEventDestroy(a->freed[i]);
+        a->ready[i] = a->freed[i] = nullptr;
+    }
+    if (a->side) cudaStreamDestroy(a->side);
+    a->side = nullptr;
     cudaFree(a->A[0]);
     cudaFree(a->A[1]);
     cudaFree(a->tug[0]);
@@ -260,6 +277,32 @@ lbm_status lbm_adjoint_create(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_eve
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) s = acuda(a, e, "cudaMemsetAsync");
     }
+    if (s == LBM_OK && a->slot.size() > 0) {
+        // optional: the second slot set, its stream and events; without them
+        // the backward runs serially
+        bool ok = cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaEventCreateWithFlags(&a->ready[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&a->freed[i], cudaEventDisableTiming) == cudaSuccess;
+        a->slot2.assign(a->slot.size(), nullptr);
+        for (auto &p : a->slot2)
+            if (ok) ok = cudaMalloc(&p, a->fbytes) == cudaSuccess;
+        for (void *p : a->slot2)
+            if (ok && p) ok = cudaMemsetAsync(p, 0, a->fbytes, c->st) == cudaSuccess;
+        if (ok) ok = cudaStreamSynchronize(c->st) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            for (void *p : a->slot2) cudaFree(p);
+            a->slot2.clear();
+            for (int i = 0; i < 2; ++i) {
+                if (a->ready[i]) cudaEventDestroy(a->ready[i]);
+                if (a->freed[i]) cudaEventDestroy(a->freed[i]);
+                a->ready[i] = a->freed[i] = nullptr;
+            }
+            if (a->side) cudaStreamDestroy(a->side);
+            a->side = nullptr;
+        }
+    }
     if (s != LBM_OK) {
         g_adj_err = a->err;
         free_all(a);
@@ -275,6 +318,7 @@ void lbm_adjoint_destroy(lbm_adjoint *a)
     if (!a) return;
     cudaSetDevice(a->c->cfg.device);
     cudaStreamSynchronize(a->c->st);
+    if (a->side) cudaStreamSynchronize(a->side);
     free_all(a);
     delete a;
 }
@@ -399,13 +443,48 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
     const long long tasks = (long long)c->L.ny * ((c->L.nx + 32 * vec - 1) / (32 * vec));
     const int grid = (int)std::max(1LL, std::min((tasks + 3) / 4, (long long)sms * per_sm));
     const long long nck = (long long)a->ck.size();
+    const bool pipe = !a->slot2.empty();
+    // slot set of segment k: with the second set, segments alternate between
+    // them, so that segment k - 1 is recomputed on the side stream while the
+    // adjoint steps of segment k run on the context's stream
+    auto slots = [&](long long k) -> std::vector<void *> & { return (pipe && (k & 1)) ? a->slot2 : a->slot; };
+    auto recompute = [&](long long k, cudaStream_t st) -> lbm_status {
+        const long long s0 = k * a->K, s1 = std::min(s0 + a->K, a->nsteps);
+        std::vector<void *> &sl = slots(k);
+        for (long long n = s0 + 1; n < s1; ++n) {
+            const void *fin = n - 1 == s0 ? a->ck[(size_t)k] : sl[(size_t)(n - 1 - s0 - 1)];
+            lbm_status r = recompute_step(a, fin, sl[(size_t)(n - s0 - 1)], n - 1, st);
+            if (r != LBM_OK) return r;
+        }
+        return LBM_OK;
+    };
+    if (pipe && nck > 0) {
+        // the side stream starts after everything queued so far; both slot
+        // sets start free
+        AK(a, cudaEventRecord(a->freed[0], c->st));
+        AK(a, cudaEventRecord(a->freed[1], c->st));
+        AK(a, cudaStreamWaitEvent(a->side, a->freed[0], 0));
+        s = recompute(nck - 1, a->side);
+        if (s != LBM_OK) return s;
+        AK(a, cudaEventRecord(a->ready[(nck - 1) & 1], a->side));
+    }
     for (long long k = nck - 1; k >= 0; --k) {
         const long long s0 = k * a->K, s1 = std::min(s0 + a->K, a->nsteps);
-        auto state = [&](long long n) -> const void * { return n == s0 ? a->ck[(size_t)k] : a->slot[(size_t)(n - s0 - 1)]; };
-        for (long long n = s0 + 1; n < s1; ++n) {
-            s = recompute_step(a, state(n - 1), a->slot[(size_t)(n - s0 - 1)], n - 1);
+        if (pipe) {
+            AK(a, cudaStreamWaitEvent(c->st, a->ready[k & 1], 0));
+            if (k > 0) {
+                // segment k - 1 into the other set once the steps that read it are done
+                AK(a, cudaStreamWaitEvent(a->side, a->freed[(k - 1) & 1], 0));
+                s = recompute(k - 1, a->side);
+                if (s != LBM_OK) return s;
+                AK(a, cudaEventRecord(a->ready[(k - 1) & 1], a->side));
+            }
+        } else {
+            s = recompute(k, c->st);
             if (s != LBM_OK) return s;
         }
+        std::vector<void *> &sl = slots(k);
+        auto state = [&](long long n) -> const void * { return n == s0 ? a->ck[(size_t)k] : sl[(size_t)(n - s0 - 1)]; };
         for (long long n = s1 - 1; n >= s0; --n) {
             s = adjoint_step(a, state(n), cur, grid);
             if (s != LBM_OK) return s;
@@ -415,6 +494,7 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
                 if (s != LBM_OK) return s;
             }
         }
+        if (pipe) AK(a, cudaEventRecord(a->freed[k & 1], c->st));
     }
     // the init (its u* and its collision included)
     AdjInitArgs ai;
