@@ -116,11 +116,12 @@ AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, int cur)
     return r;
 }
 
-lbm_status record(lbm_adjoint *a, int k)
+// sensor displacements of the state in buffer f (u* of the context)
+lbm_status record(lbm_adjoint *a, int k, const void *f)
 {
     lbm_ctx *c = a->c;
     RecordArgs r;
-    r.f = c->f[c->cur];
+    r.f = f;
     r.ustar = c->ustar;
     r.sens = a->d_sens;
     r.out = a->d_rec + (size_t)k * a->nsens * 2;
@@ -169,6 +170,28 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         s.status = a->status_scr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
         AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
+    }
+    return LBM_OK;
+}
+
+// forward step from buffer fin (state n) into fout with the context's u*
+// and status word: the step lbm_step would take, with its output placed
+// where the forward pass wants it
+lbm_status forward_step(lbm_adjoint *a, const void *fin, void *fout, long long n)
+{
+    lbm_ctx *c = a->c;
+    if (fp64(a)) {
+        StepArgs<double> s = ctx_step_args<double>(c, c->cur);
+        s.fin = fin;
+        s.fout = fout;
+        for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
+    } else {
+        StepArgs<float> s = ctx_step_args<float>(c, c->cur);
+        s.fin = fin;
+        s.fout = fout;
+        for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
+        AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, c->st));
     }
     return LBM_OK;
 }
@@ -386,17 +409,31 @@ lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t ord
     s = ctx_refresh_ghosts(c);
     if (s != LBM_OK) return afail(a, s, c->err);
     const long long n0 = c->step;  // 0 after init
-    for (long long n = 0; n <= a->nsteps; ++n) {
-        if (n > 0) {
-            s = lbm_step_async(c, 1);
-            if (s != LBM_OK) return afail(a, s, c->err);
-        }
-        if (n < a->nsteps && n % a->K == 0)
-            AK(a, cudaMemcpyAsync(a->ck[(size_t)(n / a->K)], c->f[c->cur], a->fbytes, cudaMemcpyDeviceToDevice, c->st));
+    // Each step writes its state straight into its checkpoint buffer when it
+    // is a checkpoint step, else into the context buffer it does not read,
+    // so no state is copied except f*^0; the last state lands in a context
+    // buffer, which the context then takes as current.
+    const void *in = c->f[c->cur];
+    if (a->nsteps > 0) AK(a, cudaMemcpyAsync(a->ck[0], in, a->fbytes, cudaMemcpyDeviceToDevice, c->st));
+    if (a->rec_at[0] >= 0) {
+        s = record(a, a->rec_at[0], in);
+        if (s != LBM_OK) return s;
+    }
+    if (a->nsteps > 0) in = a->ck[0];
+    for (long long n = 1; n <= a->nsteps; ++n) {
+        void *out = (n < a->nsteps && n % a->K == 0) ? a->ck[(size_t)(n / a->K)]
+                                                    : (in == c->f[0] ? c->f[1] : c->f[0]);
+        s = forward_step(a, in, out, n0 + n - 1);
+        if (s != LBM_OK) return s;
+        in = out;
         if (a->rec_at[(size_t)n] >= 0) {
-            s = record(a, a->rec_at[(size_t)n]);
+            s = record(a, a->rec_at[(size_t)n], in);
             if (s != LBM_OK) return s;
         }
+    }
+    if (a->nsteps > 0) {
+        c->cur = (in == c->f[1]) ? 1 : 0;
+        c->step = n0 + a->nsteps;
     }
     AK(a, cudaEventRecord(a->ev[1], c->st));
     s = lbm_sync(c);
