@@ -420,7 +420,8 @@ __device__ __forceinline__ void tangent_jvp_t(int law, const R F[4], const R dF[
     // NH:    dP = mu dF + lambda J^2 (H : dF) H + [mu - (lambda/2)(J^2 - 1)] H dF^T H
     // logNH: dP = mu dF + lambda     (H : dF) H + [mu - lambda log J]        H dF^T H
     const R J = F[0] * F[3] - F[1] * F[2];
-    const R H[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    const R iJ = R(1) / J;
+    const R H[4] = {F[3] * iJ, -F[2] * iJ, -F[1] * iJ, F[0] * iJ};
     const R HdF = H[0] * dF[0] + H[1] * dF[1] + H[2] * dF[2] + H[3] * dF[3];
     R a, b;
     if (law == LAW_NH) {

@@ -17,16 +17,17 @@ __device__ __forceinline__ long long pidx(const Layout &L, int q, int k, int x, 
 
 // Second-order difference of a compact field along x (dir 0) or y (dir 1):
 // central inside, wrap-around when periodic, one-sided three-point stencil at
-// a non-periodic end (Sec. 3.4).
-__device__ inline double fd(const double *a, int nx, int ny, int x, int y, int dir, int per, double dx)
+// a non-periodic end (Sec. 3.4). h = 1 / (2 dx), computed once by the caller
+// (a multiply instead of an FP64 divide per difference).
+__device__ inline double fd(const double *a, int nx, int ny, int x, int y, int dir, int per, double h)
 {
     const int n = dir == 0 ? nx : ny;
     const int i = dir == 0 ? x : y;
     auto at = [&](int j) { return dir == 0 ? a[(long long)y * nx + j] : a[(long long)j * nx + x]; };
-    if (per) return (at((i + 1) % n) - at((i - 1 + n) % n)) / (2.0 * dx);
-    if (i == 0) return (-3.0 * at(0) + 4.0 * at(1) - at(2)) / (2.0 * dx);
-    if (i == n - 1) return (3.0 * at(n - 1) - 4.0 * at(n - 2) + at(n - 3)) / (2.0 * dx);
-    return (at(i + 1) - at(i - 1)) / (2.0 * dx);
+    if (per) return (at((i + 1) % n) - at((i - 1 + n) % n)) * h;
+    if (i == 0) return (-3.0 * at(0) + 4.0 * at(1) - at(2)) * h;
+    if (i == n - 1) return (3.0 * at(n - 1) - 4.0 * at(n - 2) + at(n - 3)) * h;
+    return (at(i + 1) - at(i - 1)) * h;
 }
 
 // f^eq_q(U) - f^eq_q(U_rest) of Eq. (12): U_ofs = U - U_rest (v, F - I), P the
@@ -61,9 +62,10 @@ __device__ inline bool init_node_ofs(const InitArgs &a, int x, int y, const LawP
     feq_ofs<R>(U, P, c, f);
     if (a.order == 2) {
         R gX[6], gY[6], dPX[4], dPY[4];
+        const double h = 0.5 / a.dx;
         for (int k = 0; k < 6; ++k) {
-            gX[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 0, a.xper, a.dx);
-            gY[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, a.dx);
+            gX[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 0, a.xper, h);
+            gY[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, h);
         }
         // d_alpha P = C : d_alpha F (text after Eq. 18), as Jacobian actions (Eq. 8)
         tangent_jvp_t<R>(a.m.law, F, gX + 2, m, dPX);
