@@ -30,6 +30,8 @@ def _load():
     if _lib is None:
         path = _build.build()
         lib = C.CDLL(path)
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_threads.restype = C.c_int
         lib.orc_new.restype = C.c_void_p
         lib.orc_new.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]
         lib.orc_free.argtypes = [C.c_void_p]
@@ -80,6 +82,16 @@ def _params(prm):
     a = np.zeros(8)
     a[: len(prm)] = prm
     return a
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's per-node loops (bit-identical results
+    for any count)."""
+    _load().orc_set_threads(int(n))
+
+
+def threads():
+    return _load().orc_threads()
 
 
 # ---------------------------------------------------------------- pointwise

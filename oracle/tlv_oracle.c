@@ -8,6 +8,13 @@
  * fast-math. Only the tests, the package smoke check and the benchmark's
  * CPU-baseline leg load it. It shares no code with the CUDA sources.
  *
+ * Threads: the per-node loops of the initialization, of the phases of a step
+ * and of the read-outs run their nodes (rows, or flat node ranges) across
+ * OpenMP threads when the library is built with OpenMP. Each node's
+ * arithmetic is the same whatever the thread count and no sum runs across
+ * nodes, so every result is bit-identical for any number of threads; the
+ * edge phase and the reference adjoint stay serial.
+ *
  * Readings of points the paper leaves open (each listed in the design notes):
  *  - nodes are cell centred, so a half-way wall lies dx/2 outside the first
  *    and last node of a non-periodic direction (Sec. 3.6);
@@ -35,6 +42,28 @@
 #include <string.h>
 
 #include "tlv_oracle.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Sec. 3.1: the D2Q4 directions (i, j) */
 static const int CI[4] = {1, 0, -1, 0};
@@ -551,22 +580,24 @@ int orc_init(orc *o, const double *U0, const double *u0, int order, const double
 {
     const long N = o->N;
     const double dt = o->dt;
-    int ix, iy, q, k;
+    int iy, st = 0;
     int rc = check_edges(o);
     if (rc) return rc;
     if (o->law < 0) return -4;
     if (order != 0 && order != 2) return -5;
-    o->status = 0;
+#pragma omp parallel for schedule(static) reduction(| : st)
     for (iy = 0; iy < o->ny; ++iy)
-        for (ix = 0; ix < o->nx; ++ix) {
+        for (int ix = 0; ix < o->nx; ++ix) {
             const long n = nid(o, ix, iy);
             double f[24];
-            o->status |= init_at(o, U0, order, dUdX, dUdY, ix, iy, f);
-            for (q = 0; q < 4; ++q)
-                for (k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = f[q * 6 + k];
+            st |= init_at(o, U0, order, dUdX, dUdY, ix, iy, f);
+            for (int q = 0; q < 4; ++q)
+                for (int k = 0; k < 6; ++k) o->f[(long)(q * 6 + k) * N + n] = f[q * 6 + k];
             /* Sec. 3.5: u*^0 = u0 - (dt/2) v0 */
-            for (k = 0; k < 2; ++k) o->ustar[k * N + n] = (u0 ? u0[k * N + n] : 0.0) - 0.5 * dt * U0[k * N + n];
+            for (int k = 0; k < 2; ++k)
+                o->ustar[k * N + n] = (u0 ? u0[k * N + n] : 0.0) - 0.5 * dt * U0[k * N + n];
         }
+    o->status = st;
     o->step = 0;
     o->ready = 1;
     return 0;
@@ -689,42 +720,48 @@ int orc_step(orc *o, int nsteps)
 {
     const long N = o->N;
     const double c = o->c, dt = o->dt, w = o->omega;
-    int s, q, k, ix, iy, e;
+    int s, k, iy, e;
     if (!o->ready) return -1;
     for (s = 0; s < nsteps; ++s) {
         const double t = o->step * dt;
         long n;
+        int st = 0;
         /* 1. state recovery, Eq. (10): U^n = sum_q f_q + (dt/2) B */
+#pragma omp parallel for schedule(static)
         for (n = 0; n < N; ++n)
-            for (k = 0; k < 6; ++k) {
+            for (int k = 0; k < 6; ++k) {
                 double sum = 0.0;
-                for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
+                for (int q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
                 if (k < 2) sum += 0.5 * dt * bforce(o, k, n);
                 o->U[k * N + n] = sum;
             }
         /* 2-3. P(F^n), fluxes, equilibrium and BGK collision with the
          * trapezoidal source, Eq. (14) with w_ij = 1/8 */
+#pragma omp parallel for schedule(static) reduction(| : st)
         for (n = 0; n < N; ++n) {
             double U[6], F[4], P[4], feq[24], pb[8];
-            for (k = 0; k < 6; ++k) U[k] = o->U[k * N + n];
-            for (k = 0; k < 4; ++k) F[k] = U[2 + k];
-            if (orc_piola(o->law, node_prm(o, n, pb), F, P) != 0) o->status |= ORC_BAD_J;
-            for (k = 0; k < 6; ++k)
-                if (!isfinite(U[k])) o->status |= ORC_NONFINITE;
+            for (int k = 0; k < 6; ++k) U[k] = o->U[k * N + n];
+            for (int k = 0; k < 4; ++k) F[k] = U[2 + k];
+            if (orc_piola(o->law, node_prm(o, n, pb), F, P) != 0) st |= ORC_BAD_J;
+            for (int k = 0; k < 6; ++k)
+                if (!isfinite(U[k])) st |= ORC_NONFINITE;
             orc_feq(U, P, c, feq);
-            for (q = 0; q < 4; ++q)
-                for (k = 0; k < 6; ++k) {
+            for (int q = 0; q < 4; ++q)
+                for (int k = 0; k < 6; ++k) {
                     const long idx = (long)(q * 6 + k) * N + n;
                     const double Bk = (k < 2) ? bforce(o, k, n) : 0.0;
                     o->fs[idx] = o->f[idx] + w * (feq[q * 6 + k] - o->f[idx]) + dt * (2.0 - w) * 0.125 * Bk;
                 }
         }
+        o->status |= st;
         /* 4. streaming, Eq. (15): f_q(X + c_q dt) = f*_q(X); links that leave a
          * non-periodic domain are dropped and rebuilt in phase 5 */
+#pragma omp parallel for schedule(static)
         for (n = 0; n < 24 * N; ++n) o->f[n] = NAN;
+#pragma omp parallel for schedule(static)
         for (iy = 0; iy < o->ny; ++iy)
-            for (ix = 0; ix < o->nx; ++ix)
-                for (q = 0; q < 4; ++q) {
+            for (int ix = 0; ix < o->nx; ++ix)
+                for (int q = 0; q < 4; ++q) {
                     int tx = ix + CI[q], ty = iy + CJ[q];
                     if (tx < 0 || tx >= o->nx) {
                         if (!xper(o)) continue;
@@ -734,7 +771,7 @@ int orc_step(orc *o, int nsteps)
                         if (!yper(o)) continue;
                         ty = (ty + o->ny) % o->ny;
                     }
-                    for (k = 0; k < 6; ++k)
+                    for (int k = 0; k < 6; ++k)
                         o->f[(long)(q * 6 + k) * N + nid(o, tx, ty)] = o->fs[(long)(q * 6 + k) * N + nid(o, ix, iy)];
                 }
         /* 5. half-way reconstruction of the missing incoming populations,
@@ -775,8 +812,9 @@ int orc_step(orc *o, int nsteps)
         }
         /* 6. displacement quadrature, Eq. (22):
          * u^n = u*^n + (dt/2) v^n, u*^{n+1} = u^n + (dt/2) v^n */
+#pragma omp parallel for schedule(static)
         for (n = 0; n < N; ++n)
-            for (k = 0; k < 2; ++k) {
+            for (int k = 0; k < 2; ++k) {
                 const double un = o->ustar[k * N + n] + 0.5 * dt * o->U[k * N + n];
                 o->ustar[k * N + n] = un + 0.5 * dt * o->U[k * N + n];
             }
@@ -790,12 +828,13 @@ void orc_state(const orc *o, double *U, double *P, double *sigma)
 {
     const long N = o->N;
     long n;
-    int q, k;
+#pragma omp parallel for schedule(static)
     for (n = 0; n < N; ++n) {
         double u6[6], F[4], Pn[4], J, pb[8];
+        int k;
         for (k = 0; k < 6; ++k) {
             double sum = 0.0;
-            for (q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
+            for (int q = 0; q < 4; ++q) sum += o->f[(long)(q * 6 + k) * N + n];
             if (k < 2) sum += 0.5 * o->dt * bforce(o, k, n);
             u6[k] = sum;
             if (U) U[k * N + n] = sum;
@@ -820,11 +859,11 @@ void orc_displacement(const orc *o, double *u)
 {
     const long N = o->N;
     long n;
-    int q, k;
+#pragma omp parallel for schedule(static)
     for (n = 0; n < N; ++n)
-        for (k = 0; k < 2; ++k) {
+        for (int k = 0; k < 2; ++k) {
             double v = 0.0;
-            for (q = 0; q < 4; ++q) v += o->f[(long)(q * 6 + k) * N + n];
+            for (int q = 0; q < 4; ++q) v += o->f[(long)(q * 6 + k) * N + n];
             v += 0.5 * o->dt * bforce(o, k, n);
             u[k * N + n] = o->ustar[k * N + n] + 0.5 * o->dt * v;
         }

@@ -53,6 +53,11 @@ void   orc_flux(const double U[6], const double P[4], double PhiX[6], double Phi
 void   orc_feq(const double U[6], const double P[4], double c, double feq[24]);
 double orc_timefn(int kind, const double *tp, double t);
 
+/* ---- threads: OpenMP threads of the per-node loops (results are
+ * bit-identical for every count); n <= 0 leaves the count unchanged ---- */
+void   orc_set_threads(int n);
+int    orc_threads(void);
+
 /* ---- the lattice ---- */
 orc   *orc_new(int nx, int ny, double dx, double c, double omega);
 void   orc_free(orc *o);
