@@ -122,8 +122,7 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.status = c->d_status;
     a.L = c->L;
     const double w = c->cfg.omega;
-    a.omega = (T)w;
-    a.one_m_omega = (T)(1.0 - w);
+    relax_pair<T>(w, a.omega, a.one_m_omega);
     a.inv2c = (T)(0.5 / c->cfg.c);
     a.quarter = (T)0.25;
     a.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
@@ -730,15 +729,16 @@ static lbm_status tune_step16(lbm_ctx *c)
     StepArgs<float> a = step_args<float>(c, c->cur);
     a.ustar = us;
     a.status = st;
-    // two warm-up steps, then three rounds of three steps of each kernel,
-    // interleaved so that clock changes weigh on both alike
-    float ms[2] = {0.f, 0.f};
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    // a warm-up step of each, then three rounds of three steps of each
+    // kernel, interleaved so that clock changes weigh on both alike
+    constexpr int NK = 2;
+    float ms[NK] = {0.f, 0.f};
+    for (int v = 0; v < NK && e == cudaSuccess; ++v) {
         a.k16 = v;
         e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
     }
     for (int round = 0; round < 3 && e == cudaSuccess; ++round)
-        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        for (int v = 0; v < NK && e == cudaSuccess; ++v) {
             a.k16 = v;
             float t = 0.f;
             e = cudaEventRecord(ev[0], c->st);
@@ -749,7 +749,12 @@ static lbm_status tune_step16(lbm_ctx *c)
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
             ms[v] += t;
         }
-    if (e == cudaSuccess) c->k16 = ms[1] < ms[0] ? 1 : 0;
+    if (e == cudaSuccess) {
+        int best = 0;
+        for (int v = 1; v < NK; ++v)
+            if (ms[v] < ms[best]) best = v;
+        c->k16 = best;
+    }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     cudaFreeAsync(us, c->st);

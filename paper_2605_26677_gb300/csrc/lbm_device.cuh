@@ -136,12 +136,31 @@ struct EdgeDesc {
     const double *profile; // device, one factor per edge node, or nullptr
 };
 
+// omega and 1 - omega of the collision (Eq. 14) in the compute type T, as a
+// pair whose sum is exactly 1: with the two rounded on their own (for
+// omega = 1.95 in FP32 they sum to 1 + 6e-8) every step would scale the
+// node's state by that sum, an error that grows linearly with the step count
+// instead of as a random walk. One of the pair is rounded, the other is its
+// exact complement (Sterbenz: 1 - x is exact in T for x in [1/2, 2]).
+template <typename T>
+__host__ __device__ inline void relax_pair(double w, T &omega, T &one_m_omega)
+{
+    if (w >= 0.5) {
+        omega = (T)w;
+        one_m_omega = T(1) - omega;
+    } else {
+        one_m_omega = (T)(1.0 - w);
+        omega = T(1) - one_m_omega;
+    }
+}
+
 // T is the compute type; the populations are stored as the kernel's S
 template <typename T>
 struct StepArgs {
     const void *fin;             // post-collision populations f*^{n-1}, ghosts filled
     void *fout;                  // post-collision populations f*^n
-    double *__restrict__ ustar;  // u*, advanced by dt v^n
+    double *__restrict__ ustar;  // u*, advanced by dt v^n; nullptr (FP64, FP32 storage with a
+                                 // material field: the adjoint's recomputed steps) skips it
     int *status;                 // latched ST_* bits
     Layout L;
     T omega, one_m_omega, inv2c, quarter;

@@ -125,3 +125,56 @@ def group_errors(g, o):
         "sigma": rel(g["sigma"], o["sigma"]),
         "U": rel(g["U"], o["U"]),
     }
+
+
+# ---------------------------------------------------------------- 16-bit rounding model
+HALF_BITS = {2: 8, 3: 11}  # storage id -> significand bits: BF16 8, FP16 11
+
+
+def small_strain_modulus(law, prm):
+    """lambda + 2 mu_0 (mu_0 the small-strain shear modulus) of a closure's
+    parameters as lbm_set_material lists them: the largest factor between a
+    strain error and the stress error it makes near the rest state."""
+    if law in ("SVK", "NH", "LOGNH", "GENT"):
+        return prm[0] + 2.0 * prm[1]
+    if law == "MR":
+        return prm[0] + 4.0 * (prm[1] + prm[2])
+    if law == "YEOH":
+        return prm[0] + 4.0 * prm[1]
+    raise ValueError(law)
+
+
+def rounding_scales(U, P, c, modulus):
+    """Per-group ratio of the stored offsets' size to the group's size.
+
+    The 16-bit formats store f_q - f_rest; by Eq. (12) those offsets are of
+    the size of (U - U_rest)/4 and Phi/(2c), Phi holding v and P. Rounding
+    each stored value to a relative 2^-p once per step moves a state
+    component by about 2^-p times that size per step, as a random walk over
+    n steps; relative to a group g that is 2^-p sqrt(n) s_g with
+      s_g = ||(v, F - I, P/c)|| / ||g||      for v, F - I and the full state U,
+      s_P = s_sigma = that times (lambda + 2 mu_0) ||F - I|| / ||P|| read
+            through the stress (a strain error e gives a stress error up to
+            (lambda + 2 mu_0) e),
+      s_u = the larger of s_v and s_(F-I) (u integrates v and F is its
+            gradient).
+    U, P: (6|4, ...) arrays of the reference state (any array module with
+    .sum and elementwise ops)."""
+    import math
+
+    v2 = float((U[:2] ** 2).sum())
+    g2 = float(((U[2] - 1.0) ** 2).sum() + (U[3] ** 2).sum() + (U[4] ** 2).sum() + ((U[5] - 1.0) ** 2).sum())
+    p2 = float((P ** 2).sum())
+    u2 = float((U ** 2).sum())
+    off = math.sqrt(v2 + g2 + p2 / (c * c))
+    sv, sg = off / math.sqrt(v2), off / math.sqrt(g2)
+    sp = off * modulus / math.sqrt(p2)
+    return {"v": sv, "F-I": sg, "P": sp, "sigma": sp, "u": max(sv, sg), "U": off / math.sqrt(u2)}
+
+
+def tol_16bit(storage, steps, scales, C=1.5):
+    """Bound C 2^-p sqrt(n) s_g per group (rounding_scales). The measured
+    errors of every 16-bit parity case sit at 0.02 to 0.55 of 2^-p sqrt(n)
+    s_g, so C = 1.5 is about three times the largest of them."""
+    e = 2.0 ** -HALF_BITS[storage] * max(steps, 1) ** 0.5
+    return {g: C * e * s for g, s in scales.items()}

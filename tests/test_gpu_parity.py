@@ -9,34 +9,39 @@ full state U over all nodes and components):
   moves the oracle's own v, P and F - I by 3.5e-12, 1.7e-12 and 8e-13
   (test_oracle_conditioning); the per-group bound sits a factor three above
   that floor.
-  FP32 storage: 1e-5 on U (the paper's full-state norm); 1e-4 per group. Per
-  step each stored value is rounded once in FP32 (eps = 6e-8) and about ten
-  operations touch it, so a neutral (omega = 2) scheme accumulates about
-  10 eps sqrt(n) = 1.9e-5 after n = 1000 steps on the offsets; 1e-4 leaves a
-  factor five.
-  FP16 / BF16 storage (FP32 compute): every stored offset is rounded once per
-  step to a relative 2^-11 / 2^-8; four such values enter each state
-  component, so after n steps of a neutral scheme the group error is about
-  2 * 2^-p sqrt(n). The bounds are 4 * 2^-p sqrt(n) per group and a tenth of
-  that on U.
+  FP32 storage: 1e-5 per group (the FP32 target after 1000 steps) except the
+  displacement, and 1e-6 on U. The displacement u gets 2e-5: it integrates
+  the velocity error of every step, and in the periodic cases with a body
+  force (mean flow growing as b t, u as b t^2 / 2) the FP32 rounding of the
+  slowly varying velocity populations adds up with one sign over the run
+  (1.05e-5 after 300 steps there, where a one-ulp FP32 perturbation of the
+  start alone moves v by only 6.5e-7).
+  FP16 / BF16 storage (FP32 compute): the rounding model of
+  tests.cases.rounding_scales, 1.5 * 2^-p * sqrt(n) * s_g per group with
+  2^-p = 2^-11 / 2^-8 and s_g the ratio of the stored offsets' size to the
+  group's size, taken from the oracle's state; every case measures 0.02 to
+  0.55 of 2^-p sqrt(n) s_g.
 """
 import numpy as np
 import pytest
 
-from tests.cases import Case, group_errors, run_gpu, run_oracle, smooth_field
+from tests.cases import (Case, group_errors, rounding_scales, run_gpu, run_oracle, small_strain_modulus,
+                         smooth_field, tol_16bit)
 
 pytestmark = pytest.mark.gpu
 
 F64, F32, BF16, F16 = 0, 1, 2, 3
-TOL = {F64: dict(group=1e-11, U=1e-12), F32: dict(group=1e-4, U=1e-5)}
-HALF_BITS = {F16: 11, BF16: 8}
+TOL = {F64: dict(group=1e-11, U=1e-12), F32: dict(group=1e-5, u=2e-5, U=1e-6)}
 
 
-def tol_for(storage, steps):
+def tol_for(storage, steps, ref=None, c=5.0, modulus=None):
+    """Per-group bounds {group: bound} (see the module docstring); the 16-bit
+    bounds need the reference state ref = {"U": U, "P": P} and the
+    closure's lambda + 2 mu_0."""
     if storage in TOL:
-        return TOL[storage]
-    g = 4.0 * 2.0 ** -HALF_BITS[storage] * max(steps, 1) ** 0.5
-    return dict(group=g, U=0.1 * g)
+        t = TOL[storage]
+        return {g: t.get(g, t["group"]) for g in ("v", "F-I", "P", "u", "sigma")} | {"U": t["U"]}
+    return tol_16bit(storage, steps, rounding_scales(ref["U"], ref["P"], c, modulus))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,12 +58,13 @@ def check(case, storage, skip=()):
     g = run_gpu(case, storage)
     o = run_oracle(case)
     errs = group_errors(g, o)
-    tol = tol_for(storage, case.steps)
+    print("PARITY storage=%d steps=%d %dx%d" % (storage, case.steps, case.nx, case.ny),
+          {k: "%.2e" % v for k, v in errs.items()})
+    tol = tol_for(storage, case.steps, o, case.c, small_strain_modulus(case.law, case.material()))
     for k, v in errs.items():
         if k in skip:
             continue
-        lim = tol["U"] if k == "U" else tol["group"]
-        assert v <= lim, (k, v, errs)
+        assert v <= tol[k], (k, v, tol[k], errs)
     assert abs(g["t"] - o["t"]) < 1e-12
     return errs
 
@@ -275,9 +281,10 @@ def test_edge_data_changed_between_steps(storage, fb_mode):
     O.step(n2)
     Uo, Po, So = O.state()
     errs = group_errors({"U": U, "P": P, "u": u, "sigma": S}, {"U": Uo, "P": Po, "u": O.displacement(), "sigma": So})
-    tol = TOL[storage]
+    print("PARITY edge data changed, storage=%d" % storage, {k: "%.2e" % v for k, v in errs.items()})
+    tol = tol_for(storage, n1 + n2)
     for k, v in errs.items():
-        assert v <= (tol["U"] if k == "U" else tol["group"]), (k, v, errs)
+        assert v <= tol[k], (k, v, errs)
 
 
 @pytest.mark.parametrize("storage", [F64, F32])
@@ -321,10 +328,10 @@ def test_tabulated_time_function(storage):
         O.step(1)
     Uo, Po, So = O.state()
     errs = group_errors({"U": U, "P": P, "u": u, "sigma": So}, {"U": Uo, "P": Po, "u": O.displacement(), "sigma": So})
-    tol = TOL[storage]
-    for k in ("v", "F-I", "P", "u"):
-        assert errs[k] <= tol["group"], (k, errs)
-    assert errs["U"] <= tol["U"], errs
+    print("PARITY tabulated load, storage=%d" % storage, {k: "%.2e" % v for k, v in errs.items()})
+    tol = tol_for(storage, steps)
+    for k in ("v", "F-I", "P", "u", "U"):
+        assert errs[k] <= tol[k], (k, errs)
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16, BF16])
