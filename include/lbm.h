@@ -261,7 +261,11 @@ double lbm_bytes_per_node_update(const lbm_ctx *ctx);
  * lbm_read_state_device) into the caller's out_dev (device, 10 doubles, the
  * layout of lbm_diagnostics) for closure `law` with its params (as
  * lbm_set_material lists them) and spacing dx, on `stream` of `device`,
- * without waiting.
+ * without waiting. The material is uniform: for a context with a per-node
+ * shear-modulus field (lbm_set_material_field) the energy out[6] is that of
+ * the uniform params passed here, not of the field (the other nine entries
+ * do not depend on the material). The call makes `device` current while it
+ * runs and restores the calling thread's current device before it returns.
  * Its block partials live in one fixed 1.25 MiB array in the library's device
  * memory (held on every GPU that loads the library until the process exits),
  * so a call takes at most 67,108,864 nodes (8192^2) and returns LBM_ERR_ARG

@@ -14,7 +14,9 @@
 // All calls share the array: two calls whose kernels overlap on the GPU (on
 // different streams, or on one stream from different host threads) race on
 // it. Each call overwrites every slot it later reads, so nothing needs
-// clearing between calls.
+// clearing between calls. The material is the uniform closure the caller
+// names; the call makes `device` current only while it runs and gives the
+// calling thread back its previous current device on every return.
 #include <cfloat>
 #include <mutex>
 #include <string>
@@ -171,6 +173,22 @@ lbm_status noalloc_fail(lbm_status s, const std::string &msg)
     return s;
 }
 
+// restores the calling thread's current device when the call returns
+struct DeviceRestore {
+    int prev = -1;
+    DeviceRestore()
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            cudaGetLastError();
+        }
+    }
+    ~DeviceRestore()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 } // namespace
 
 extern "C" lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t nx, int32_t ny, int32_t law,
@@ -189,6 +207,7 @@ extern "C" lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t
     if (!params || nparams < need[law]) return noalloc_fail(LBM_ERR_ARG, "too few closure parameters");
     if (!(dx > 0.0)) return noalloc_fail(LBM_ERR_ARG, "dx must be > 0");
     if (device < 0 || device >= NOALLOC_MAX_DEVICES) return noalloc_fail(LBM_ERR_ARG, "device ordinal out of range");
+    DeviceRestore restore_;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return noalloc_fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     double *partial;

@@ -31,14 +31,18 @@ def lbm():
     return m
 
 
+LAWS = {"NH": (1, [1.5, 0.75]), "MR": (3, [1.5, 0.25, 0.125]), "GENT": (5, [1.5, 0.75, 10.0])}
+
+
+@pytest.mark.parametrize("law", sorted(LAWS))
 @pytest.mark.parametrize("storage", [0, 1])
-def test_noalloc_diagnostics_match_existing_entry_point(lbm, storage):
+def test_noalloc_diagnostics_match_existing_entry_point(lbm, storage, law):
     import torch
 
     nx, ny = 301, 157  # several reduction blocks and a ragged last block
     L = lbm.Lattice(nx, ny, storage=storage, omega=1.9)
-    lam, mu = 1.5, 0.75
-    lbm.lbm_set_material(L.ctx, lbm.LBM_LAW_NH, [lam, mu])
+    law_id, prm = LAWS[law]
+    lbm.lbm_set_material(L.ctx, law_id, prm)
     lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
     lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.01))
     lbm.lbm_init(L.ctx, smooth_field(nx, ny, seed=41, amp=0.05, periodic=False))
@@ -47,12 +51,15 @@ def test_noalloc_diagnostics_match_existing_entry_point(lbm, storage):
     U = torch.empty((6, ny, nx), dtype=torch.float64, device="cuda")
     lbm.lbm_read_state_device(L.ctx, U)
     lbm.lbm_sync(L.ctx)
+    dev = torch.cuda.current_device()
     for _ in range(2):
         out = torch.full((10,), float("nan"), dtype=torch.float64, device="cuda")
-        lbm.lbm_diagnostics_state_noalloc(U, nx, ny, lbm.LBM_LAW_NH, [lam, mu], 1.0, out)
+        lbm.lbm_diagnostics_state_noalloc(U, nx, ny, law_id, prm, 1.0, out)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.allclose(got, expect, rtol=1e-11, atol=1e-13), (got, expect)
+        # the call leaves the calling thread's current device as it was
+        assert torch.cuda.current_device() == dev
     L.close()
 
 
