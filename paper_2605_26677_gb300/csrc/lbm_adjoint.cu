@@ -41,7 +41,6 @@ struct lbm_adjoint {
     void *tug[2] = {nullptr, nullptr};  // traction-edge cotangent of G, compute type, 4 planes (u* layout)
     void *ubar = nullptr;      // compute type, 2 planes (u* layout)
     double *gmu = nullptr;     // plane (u* layout)
-    double *ustar_scr = nullptr;
     int *status_scr = nullptr;
     double *U0 = nullptr;      // copy of the initial state (6N)
     double *ghat = nullptr;    // 4N
@@ -105,9 +104,10 @@ AdjArgs<T> adj_args(const lbm_adjoint *a, const void *fin, int cur)
     r.ubar = static_cast<const T *>(a->ubar);
     r.gmu = a->gmu;
     r.L = c->L;
-    r.one_m_omega = (T)(1.0 - w);
-    r.wq = (T)(0.25 * w);
-    r.wi2c = (T)(0.5 * w / c->cfg.c);
+    T wT;
+    relax_pair<T>(w, wT, r.one_m_omega);  // the forward's pair (transposed collision)
+    r.wq = T(0.25) * wT;
+    r.wi2c = (T)(0.5 * (double)wT / c->cfg.c);
     r.wi2c_d = 0.5 * w / c->cfg.c;
     r.dtT = (T)c->dt;
     r.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
@@ -149,8 +149,9 @@ lbm_status inject(lbm_adjoint *a, void *aout, int k)
     return LBM_OK;
 }
 
-// one forward step from buffer fin (state n) into fout, u* and status into
-// scratch, on stream st
+// one forward step from buffer fin (state n) into fout, without the
+// displacement quadrature (the recomputed states need only their
+// populations) and with the status word in scratch, on stream st
 lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long n, cudaStream_t st)
 {
     lbm_ctx *c = a->c;
@@ -158,7 +159,7 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         StepArgs<double> s = ctx_step_args<double>(c, c->cur);
         s.fin = fin;
         s.fout = fout;
-        s.ustar = a->ustar_scr;
+        s.ustar = nullptr;
         s.status = a->status_scr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
         AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
@@ -166,7 +167,7 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         StepArgs<float> s = ctx_step_args<float>(c, c->cur);
         s.fin = fin;
         s.fout = fout;
-        s.ustar = a->ustar_scr;
+        s.ustar = nullptr;
         s.status = a->status_scr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
         AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
@@ -230,7 +231,6 @@ void free_all(lbm_adjoint *a)
     cudaFree(a->tug[1]);
     cudaFree(a->ubar);
     cudaFree(a->gmu);
-    cudaFree(a->ustar_scr);
     cudaFree(a->status_scr);
     cudaFree(a->U0);
     cudaFree(a->ghat);
@@ -285,15 +285,13 @@ lbm_status lbm_adjoint_create(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_eve
     alloc(&a->tug[1], (size_t)4 * c->L.uplane * R);
     alloc(&a->ubar, (size_t)2 * c->L.uplane * R);
     alloc((void **)&a->gmu, (size_t)c->L.uplane * sizeof(double));
-    alloc((void **)&a->ustar_scr, (size_t)2 * c->L.uplane * sizeof(double));
     alloc((void **)&a->status_scr, sizeof(int));
     alloc((void **)&a->U0, 6 * N * sizeof(double));
     alloc((void **)&a->ghat, 4 * N * sizeof(double));
     for (cudaEvent_t &ev : a->ev)
         if (s == LBM_OK && cudaEventCreate(&ev) != cudaSuccess) s = afail(a, LBM_ERR_CUDA, "cudaEventCreate");
     if (s == LBM_OK) {
-        e = cudaMemsetAsync(a->ustar_scr, 0, (size_t)2 * c->L.uplane * sizeof(double), c->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(a->status_scr, 0, sizeof(int), c->st);
+        e = cudaMemsetAsync(a->status_scr, 0, sizeof(int), c->st);
         // slots and adjoint buffers: ghosts and padding start defined
         for (void *p : a->slot)
             if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, a->fbytes, c->st);
@@ -390,16 +388,11 @@ lbm_status lbm_adjoint_set_loss(lbm_adjoint *a, int32_t nsens, const int32_t *se
     return LBM_OK;
 }
 
-lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t order, double *loss)
+namespace {
+
+lbm_status forward_body(lbm_adjoint *a, const double *U0_dev, int32_t order, double *loss)
 {
-    Range range_("lbm_adjoint_forward");
-    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
-    if (!loss) return afail(a, LBM_ERR_ARG, "loss is NULL");
-    if (a->nsens < 1) return afail(a, LBM_ERR_STATE, "lbm_adjoint_set_loss must come first");
     lbm_ctx *c = a->c;
-    if (!c->m.mufield) return afail(a, LBM_ERR_STATE, "the context lost its material field");
-    AK(a, cudaSetDevice(c->cfg.device));
-    a->forward_done = false;
     const size_t N = (size_t)c->L.nx * c->L.ny;
     AK(a, cudaEventRecord(a->ev[0], c->st));
     lbm_status s = lbm_init_device(c, U0_dev, nullptr, order);
@@ -452,15 +445,30 @@ lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t ord
     return LBM_OK;
 }
 
-lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
+} // namespace
+
+lbm_status lbm_adjoint_forward(lbm_adjoint *a, const double *U0_dev, int32_t order, double *loss)
 {
-    Range range_("lbm_adjoint_backward");
+    Range range_("lbm_adjoint_forward");
     if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
-    if (!g_mu_dev || !g_v0_dev) return afail(a, LBM_ERR_ARG, "output pointers must be non-NULL");
+    if (!loss) return afail(a, LBM_ERR_ARG, "loss is NULL");
+    if (a->nsens < 1) return afail(a, LBM_ERR_STATE, "lbm_adjoint_set_loss must come first");
     lbm_ctx *c = a->c;
-    if (!a->forward_done || c->step != a->fwd_step)
-        return afail(a, LBM_ERR_STATE, "lbm_adjoint_forward must precede, with no other step of the context between");
+    if (!c->m.mufield) return afail(a, LBM_ERR_STATE, "the context lost its material field");
     AK(a, cudaSetDevice(c->cfg.device));
+    a->forward_done = false;
+    lbm_status s = forward_body(a, U0_dev, order, loss);
+    // a failure part way leaves the context's buffers holding a partial run
+    // that its time level no longer describes: it needs a new lbm_init
+    if (s != LBM_OK) c->initialized = false;
+    return s;
+}
+
+namespace {
+
+lbm_status backward_body(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
+{
+    lbm_ctx *c = a->c;
     const int R = fp64(a) ? 8 : 4;
     AK(a, cudaEventRecord(a->ev[2], c->st));
     AK(a, cudaMemsetAsync(a->A[0], 0, a->fbytes, c->st));
@@ -564,6 +572,29 @@ lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_d
     AK(a, cudaEventRecord(a->ev[3], c->st));
     AK(a, cudaStreamSynchronize(c->st));
     return LBM_OK;
+}
+
+} // namespace
+
+lbm_status lbm_adjoint_backward(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
+{
+    Range range_("lbm_adjoint_backward");
+    if (!a) return afail(nullptr, LBM_ERR_ARG, "null adjoint");
+    if (!g_mu_dev || !g_v0_dev) return afail(a, LBM_ERR_ARG, "output pointers must be non-NULL");
+    lbm_ctx *c = a->c;
+    if (!a->forward_done || c->step != a->fwd_step)
+        return afail(a, LBM_ERR_STATE, "lbm_adjoint_forward must precede, with no other step of the context between");
+    AK(a, cudaSetDevice(c->cfg.device));
+    lbm_status s = backward_body(a, g_mu_dev, g_v0_dev);
+    if (s != LBM_OK && !a->slot2.empty()) {
+        // recomputation may still be queued on the side stream, reading the
+        // checkpoints: order the context's stream after it, so that work
+        // enqueued next on the context (a forward rewriting the checkpoints)
+        // cannot overtake it
+        if (cudaEventRecord(a->freed[0], a->side) == cudaSuccess) cudaStreamWaitEvent(c->st, a->freed[0], 0);
+        cudaGetLastError();
+    }
+    return s;
 }
 
 lbm_status lbm_adjoint_info(const lbm_adjoint *a, int32_t *checkpoint_every, int64_t *stored_states,

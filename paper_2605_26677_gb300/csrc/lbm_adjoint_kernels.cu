@@ -87,9 +87,216 @@ __device__ __forceinline__ void traction_ift(int e, const T Gb[4], const T hd[6]
 }
 
 // ---------------------------------------------------------------- main
+// The part of an adjoint task after its inputs are in registers: U^{n+1}
+// recovered from the pulled f*^n (U), a^{n+1} at the lane's nodes (h, which
+// is overwritten by the cotangents h_q), mu, ubar and the dL/dmu accumulator
+// of the lane's nodes. Adds the traction nodes' carried cotangent, applies
+// the transposed collision, pushes a^n to the pulling neighbours, applies
+// the transposed edge rules and stores dL/dmu.
+template <typename S, int LAW, int VEC>
+__device__ __forceinline__ void adj_finish(const AdjArgs<typename Prec<S>::R> &a, int y, int x0, int lane,
+                                           typename Prec<S>::R (&U)[6][VEC], typename Prec<S>::R (&h)[4][6][VEC],
+                                           const Pack<typename Prec<S>::R, VEC> &mu,
+                                           const Pack<typename Prec<S>::R, VEC> &ub0,
+                                           const Pack<typename Prec<S>::R, VEC> &ub1, Pack<double, VEC> gm)
+{
+    using T = typename Prec<S>::R;
+    using PK = Pack<S, VEC>;
+    using PD = Pack<double, VEC>;
+    const int nx = a.L.nx, ny = a.L.ny;
+    const long long plane = a.L.plane;
+    const int pitch = a.L.pitch;
+    const S *__restrict__ fin = static_cast<const S *>(a.fin);
+    S *__restrict__ aout = static_cast<S *>(a.aout);
+    const bool act = x0 < nx;
+    const long long row = (long long)(y + 1) * pitch + a.L.xoff + x0;
+    const long long urow = (long long)y * a.L.upitch + x0;
+    // the traction edges' cotangent of U at their nodes, left by the
+    // previous (later-in-time) step for every q
+    if (act) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (x0 + e < nx && on_traction(a.kind, x0 + e, y, nx, ny))
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const T u = a.tug_in[m * a.L.uplane + urow + e];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) h[q][2 + m][e] += u;
+                }
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        T Sa[6], bX[6], bY[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            Sa[k] = (h[0][k][e] + h[2][k][e]) + (h[1][k][e] + h[3][k][e]);
+            bX[k] = h[0][k][e] - h[2][k][e];
+            bY[k] = h[1][k][e] - h[3][k][e];
+        }
+        const T G[4] = {U[2][e], U[3][e], U[4][e], U[5][e]};
+        const T M[4] = {bX[0], bY[0], bX[1], bY[1]};  // cotangent of (P11, P12, P21, P22)
+        const LawP<T> mp{a.lam_ratio * mu.v[e], mu.v[e], T(0), T(0)};
+        const LawP<T> unit{a.lam_ratio, T(1), T(0), T(0)};  // d(lambda, mu)/dmu
+        T CM[4], Pm[4], dJ;
+        jvp_ofs<LAW, T>(G, M, mp, CM);
+        piola_ofs<LAW, T>(G[0], G[1], G[2], G[3], unit, Pm[0], Pm[1], Pm[2], Pm[3], dJ);
+        T g[6];
+        g[0] = a.wq * Sa[0] - a.wi2c * (bX[2] + bY[3]) + a.dtT * ub0.v[e];
+        g[1] = a.wq * Sa[1] - a.wi2c * (bX[4] + bY[5]) + a.dtT * ub1.v[e];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[2 + j] = a.wq * Sa[2 + j] - a.wi2c * CM[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[q][k][e] = a.one_m_omega * h[q][k][e] + g[k];
+        if (x0 + e < nx)
+            gm.v[e] -= a.wi2c_d * ((double)M[0] * Pm[0] + (double)M[1] * Pm[1] + (double)M[2] * Pm[2] +
+                                   (double)M[3] * Pm[3]);
+    }
+
+    // pushes: a^n_q(x - e_q) = h_q(x); what would leave the domain is
+    // handled by the edge rules below
+    const bool full = act && x0 + VEC <= nx;
+    const bool ylo = (y == 0), yhi = (y == ny - 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        // q = 1 to row y - 1 and q = 3 to row y + 1, inside the domain
+        if (act) {
+            S *d1 = aout + (1 * 6 + k) * plane + row - pitch;
+            S *d3 = aout + (3 * 6 + k) * plane + row + pitch;
+            if (full) {
+                PK o1, o3;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    o1.v[e] = to_store<S>(h[1][k][e]);
+                    o3.v[e] = to_store<S>(h[3][k][e]);
+                }
+                if (!ylo) *reinterpret_cast<PK *>(d1) = o1;
+                if (!yhi) *reinterpret_cast<PK *>(d3) = o3;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (x0 + e < nx) {
+                        if (!ylo) d1[e] = to_store<S>(h[1][k][e]);
+                        if (!yhi) d3[e] = to_store<S>(h[3][k][e]);
+                    }
+            }
+        }
+        // q = 0 to column x - 1: position p = x0 + e takes h_0(p + 1), p <= nx - 2
+        {
+            const T nxt = __shfl_down_sync(FULL_MASK, h[0][k][0], 1);
+            S *d0 = aout + (0 * 6 + k) * plane + row;
+            bool all = true;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) all = all && (x0 + e <= nx - 2) && !(lane == 31 && e == VEC - 1);
+            if (all) {
+                PK o;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) o.v[e] = to_store<S>(e < VEC - 1 ? h[0][k][e + 1] : nxt);
+                *reinterpret_cast<PK *>(d0) = o;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (x0 + e <= nx - 2 && !(lane == 31 && e == VEC - 1))
+                        d0[e] = to_store<S>(e < VEC - 1 ? h[0][k][e + 1] : nxt);
+            }
+            if (lane == 0 && act && x0 >= 1) d0[-1] = to_store<S>(h[0][k][0]);  // the previous segment's last position
+        }
+        // q = 2 to column x + 1: position p = x0 + e takes h_2(p - 1), 1 <= p <= nx - 1
+        {
+            const T prv = __shfl_up_sync(FULL_MASK, h[2][k][VEC - 1], 1);
+            S *d2 = aout + (2 * 6 + k) * plane + row;
+            bool all = true;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) all = all && (x0 + e >= 1) && (x0 + e <= nx - 1) && !(lane == 0 && e == 0);
+            if (all) {
+                PK o;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) o.v[e] = to_store<S>(e == 0 ? prv : h[2][k][e - 1]);
+                *reinterpret_cast<PK *>(d2) = o;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (x0 + e >= 1 && x0 + e <= nx - 1 && !(lane == 0 && e == 0))
+                        d2[e] = to_store<S>(e == 0 ? prv : h[2][k][e - 1]);
+            }
+            if (lane == 31 && x0 + VEC <= nx - 1) d2[VEC] = to_store<S>(h[2][k][VEC - 1]);  // the next segment's first
+        }
+    }
+
+    // Edge rules, transposed (Eqs. 23-25), at the lane's boundary nodes.
+    // The node x_b pulled f_d(x_b) = D f*_{-d}(x_b) + S_d(U^n(x_b)) (or, on a
+    // periodic edge, the opposite node's f*_d), so its h_d goes to
+    // a^n_{-d}(x_b) with D (or back to that opposite node). A traction
+    // edge adds the implicit-function derivative of F^b, which reaches
+    // every q of x_b through U^n = sum_q f*^n_q: its F-part is left in
+    // tug_out for the next step to add, and its mu-part goes to dL/dmu.
+    // No other thread writes the cells written here.
+    if (act && (ylo || yhi || x0 == 0 || x0 + VEC >= nx)) {
+        T ug[VEC][4];
+        bool tr[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            tr[e] = false;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) ug[e][m] = T(0);
+        }
+#pragma unroll
+        for (int ed = 0; ed < 4; ++ed) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int x = x0 + e;
+                if (x >= nx) continue;
+                const bool on = (ed == EDGE_LEFT) ? x == 0 : (ed == EDGE_RIGHT) ? x == nx - 1 : (ed == EDGE_BOTTOM) ? ylo : yhi;
+                if (!on) continue;
+                const int d = edge_dmiss(ed), md = edge_dout(ed);
+                T hd[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hd[k] = h[d][k][e];
+                if (a.kind[ed] == BC_PERIODIC) {
+                    const int tx = (ed == EDGE_LEFT) ? nx - 1 : (ed == EDGE_RIGHT) ? 0 : x;
+                    const int ty = (ed == EDGE_BOTTOM) ? ny - 1 : (ed == EDGE_TOP) ? 0 : y;
+                    const long long cell = (long long)(ty + 1) * pitch + a.L.xoff + tx;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) aout[(d * 6 + k) * plane + cell] = to_store<S>(hd[k]);
+                    continue;
+                }
+                const T sv = (a.kind[ed] == BC_VELOCITY) ? T(-1) : T(1);  // D on (v1, v2); -sv on F
+#pragma unroll
+                for (int k = 0; k < 6; ++k) aout[(md * 6 + k) * plane + row + e] = to_store<S>((k < 2 ? sv : -sv) * hd[k]);
+                if (a.kind[ed] != BC_TRACTION) continue;
+                tr[e] = true;
+                // the forward stored ghost = -f*_{-d} + G^b / 2 on the F-components
+                int gx, gy;
+                ghost_cell(ed, (ed <= EDGE_RIGHT) ? y : x, nx, ny, gx, gy);
+                const long long gcell = (long long)(gy + 1) * pitch + a.L.xoff + gx;
+                T Gb[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    Gb[m] = T(2) * (ld_r(fin[(d * 6 + 2 + m) * plane + gcell]) + ld_r(fin[(md * 6 + 2 + m) * plane + row + e]));
+                T dmu;
+                traction_ift<LAW, T>(ed, Gb, hd, mu.v[e], a.lam_ratio, ug[e], dmu);
+                gm.v[e] += (double)dmu;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (tr[e])
+#pragma unroll
+                for (int m = 0; m < 4; ++m) a.tug_out[m * a.L.uplane + urow + e] = ug[e][m];
+    }
+    if (act) *reinterpret_cast<PD *>(a.gmu + urow) = gm;
+}
+
+// FP32: every load of a task is issued before the shifts and sums that use
+// them (about 13.6 KB per warp in flight at once; 127 registers, 4 blocks
+// per SM), which cut the backward step by 3% against loading and summing
+// one component at a time. FP64 keeps the component-at-a-time order: its
+// loads would need twice the registers.
 template <typename S, int LAW, int VEC>
 __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjArgs<typename Prec<S>::R> a)
 {
+    constexpr bool EARLY = sizeof(S) == 4;
     pdl_enter();
     using T = typename Prec<S>::R;
     using PK = Pack<S, VEC>;
@@ -106,7 +313,6 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjAr
     const int pitch = a.L.pitch;
     const S *__restrict__ fin = static_cast<const S *>(a.fin);
     const S *__restrict__ ain = static_cast<const S *>(a.ain);
-    S *__restrict__ aout = static_cast<S *>(a.aout);
 
     for (int task = gw; task < ntask; task += nw) {
         int y, seg;
@@ -115,29 +321,107 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjAr
         const bool act = x0 < nx;
         const bool ld0 = x0 <= nx;
         const long long row = (long long)(y + 1) * pitch + a.L.xoff + x0;
+        const long long urow = (long long)y * a.L.upitch + x0;
 
-        // U^{n+1} of the lane's nodes from the pulled populations
         T U[6][VEC];
+        T h[4][6][VEC];
+        PT mu = {}, ub0 = {}, ub1 = {};
+        PD gm = {};
+        if constexpr (EARLY) {
+            // every load of the task first, so that all of them are in flight
+            // together, then the shifts and sums
+            PK c0[6], c1[6], c2[6], c3[6], av[4][6];
+            T lft[6], rgt[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            PK c0 = {}, c1 = {}, c2 = {}, c3 = {};
-            if (ld0) {
-                c0 = *reinterpret_cast<const PK *>(fin + (0 * 6 + k) * plane + row);
-                c2 = *reinterpret_cast<const PK *>(fin + (2 * 6 + k) * plane + row);
+            for (int k = 0; k < 6; ++k) {
+                c0[k] = PK{};
+                c1[k] = PK{};
+                c2[k] = PK{};
+                c3[k] = PK{};
+                lft[k] = T(0);
+                rgt[k] = T(0);
+                if (ld0) {
+                    c0[k] = *reinterpret_cast<const PK *>(fin + (0 * 6 + k) * plane + row);
+                    c2[k] = *reinterpret_cast<const PK *>(fin + (2 * 6 + k) * plane + row);
+                }
+                if (act) {
+                    c1[k] = *reinterpret_cast<const PK *>(fin + (1 * 6 + k) * plane + row - pitch);
+                    c3[k] = *reinterpret_cast<const PK *>(fin + (3 * 6 + k) * plane + row + pitch);
+                    if (lane == 0) lft[k] = ld_r(fin[(0 * 6 + k) * plane + row - 1]);
+                    if (lane == 31) rgt[k] = ld_r(fin[(2 * 6 + k) * plane + row + VEC]);
+                }
             }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    av[q][k] = PK{};
+                    if (act) av[q][k] = *reinterpret_cast<const PK *>(ain + (q * 6 + k) * plane + row);
+                }
             if (act) {
-                c1 = *reinterpret_cast<const PK *>(fin + (1 * 6 + k) * plane + row - pitch);
-                c3 = *reinterpret_cast<const PK *>(fin + (3 * 6 + k) * plane + row + pitch);
+                mu = *reinterpret_cast<const PT *>(a.mufield + urow);
+                ub0 = *reinterpret_cast<const PT *>(a.ubar + urow);
+                ub1 = *reinterpret_cast<const PT *>(a.ubar + a.L.uplane + urow);
+                gm = *reinterpret_cast<const PD *>(a.gmu + urow);
             }
-            T left = __shfl_up_sync(FULL_MASK, ld_r(c0.v[VEC - 1]), 1);
-            T right = __shfl_down_sync(FULL_MASK, ld_r(c2.v[0]), 1);
-            if (act && lane == 0) left = ld_r(fin[(0 * 6 + k) * plane + row - 1]);
-            if (act && lane == 31) right = ld_r(fin[(2 * 6 + k) * plane + row + VEC]);
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                const T f0 = (e == 0) ? left : ld_r(c0.v[e - 1]);
-                const T f2 = (e == VEC - 1) ? right : ld_r(c2.v[e + 1]);
-                U[k][e] = (f0 + f2) + (ld_r(c1.v[e]) + ld_r(c3.v[e]));
+            for (int k = 0; k < 6; ++k) {
+                T left = __shfl_up_sync(FULL_MASK, ld_r(c0[k].v[VEC - 1]), 1);
+                T right = __shfl_down_sync(FULL_MASK, ld_r(c2[k].v[0]), 1);
+                if (act && lane == 0) left = lft[k];
+                if (act && lane == 31) right = rgt[k];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const T f0 = (e == 0) ? left : ld_r(c0[k].v[e - 1]);
+                    const T f2 = (e == VEC - 1) ? right : ld_r(c2[k].v[e + 1]);
+                    U[k][e] = (f0 + f2) + (ld_r(c1[k].v[e]) + ld_r(c3[k].v[e]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) h[q][k][e] = ld_r(av[q][k].v[e]);
+        } else {
+            // U^{n+1} of the lane's nodes from the pulled populations
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                PK c0 = {}, c1 = {}, c2 = {}, c3 = {};
+                if (ld0) {
+                    c0 = *reinterpret_cast<const PK *>(fin + (0 * 6 + k) * plane + row);
+                    c2 = *reinterpret_cast<const PK *>(fin + (2 * 6 + k) * plane + row);
+                }
+                if (act) {
+                    c1 = *reinterpret_cast<const PK *>(fin + (1 * 6 + k) * plane + row - pitch);
+                    c3 = *reinterpret_cast<const PK *>(fin + (3 * 6 + k) * plane + row + pitch);
+                }
+                T left = __shfl_up_sync(FULL_MASK, ld_r(c0.v[VEC - 1]), 1);
+                T right = __shfl_down_sync(FULL_MASK, ld_r(c2.v[0]), 1);
+                if (act && lane == 0) left = ld_r(fin[(0 * 6 + k) * plane + row - 1]);
+                if (act && lane == 31) right = ld_r(fin[(2 * 6 + k) * plane + row + VEC]);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const T f0 = (e == 0) ? left : ld_r(c0.v[e - 1]);
+                    const T f2 = (e == VEC - 1) ? right : ld_r(c2.v[e + 1]);
+                    U[k][e] = (f0 + f2) + (ld_r(c1.v[e]) + ld_r(c3.v[e]));
+                }
+            }
+            // a^{n+1} at the lane's own nodes; h overwrites it in place
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    PK v = {};
+                    if (act) v = *reinterpret_cast<const PK *>(ain + (q * 6 + k) * plane + row);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) h[q][k][e] = ld_r(v.v[e]);
+                }
+            if (act) {
+                mu = *reinterpret_cast<const PT *>(a.mufield + urow);
+                ub0 = *reinterpret_cast<const PT *>(a.ubar + urow);
+                ub1 = *reinterpret_cast<const PT *>(a.ubar + a.L.uplane + urow);
+                gm = *reinterpret_cast<const PD *>(a.gmu + urow);
             }
         }
 #pragma unroll
@@ -145,202 +429,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjAr
             U[0][e] += a.hdtb1;
             U[1][e] += a.hdtb2;
         }
-
-        // a^{n+1} at the lane's own nodes; h overwrites it in place
-        T h[4][6][VEC];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                PK v = {};
-                if (act) v = *reinterpret_cast<const PK *>(ain + (q * 6 + k) * plane + row);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) h[q][k][e] = ld_r(v.v[e]);
-            }
-        const long long urow = (long long)y * a.L.upitch + x0;
-        // the traction edges' cotangent of U at their nodes, left by the
-        // previous (later-in-time) step for every q
-        if (act) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (x0 + e < nx && on_traction(a.kind, x0 + e, y, nx, ny))
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const T u = a.tug_in[m * a.L.uplane + urow + e];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) h[q][2 + m][e] += u;
-                    }
-        }
-        PT mu = {}, ub0 = {}, ub1 = {};
-        PD gm = {};
-        if (act) {
-            mu = *reinterpret_cast<const PT *>(a.mufield + urow);
-            ub0 = *reinterpret_cast<const PT *>(a.ubar + urow);
-            ub1 = *reinterpret_cast<const PT *>(a.ubar + a.L.uplane + urow);
-            gm = *reinterpret_cast<const PD *>(a.gmu + urow);
-        }
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            T Sa[6], bX[6], bY[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                Sa[k] = (h[0][k][e] + h[2][k][e]) + (h[1][k][e] + h[3][k][e]);
-                bX[k] = h[0][k][e] - h[2][k][e];
-                bY[k] = h[1][k][e] - h[3][k][e];
-            }
-            const T G[4] = {U[2][e], U[3][e], U[4][e], U[5][e]};
-            const T M[4] = {bX[0], bY[0], bX[1], bY[1]};  // cotangent of (P11, P12, P21, P22)
-            const LawP<T> mp{a.lam_ratio * mu.v[e], mu.v[e], T(0), T(0)};
-            const LawP<T> unit{a.lam_ratio, T(1), T(0), T(0)};  // d(lambda, mu)/dmu
-            T CM[4], Pm[4], dJ;
-            jvp_ofs<LAW, T>(G, M, mp, CM);
-            piola_ofs<LAW, T>(G[0], G[1], G[2], G[3], unit, Pm[0], Pm[1], Pm[2], Pm[3], dJ);
-            T g[6];
-            g[0] = a.wq * Sa[0] - a.wi2c * (bX[2] + bY[3]) + a.dtT * ub0.v[e];
-            g[1] = a.wq * Sa[1] - a.wi2c * (bX[4] + bY[5]) + a.dtT * ub1.v[e];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) g[2 + j] = a.wq * Sa[2 + j] - a.wi2c * CM[j];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k = 0; k < 6; ++k) h[q][k][e] = a.one_m_omega * h[q][k][e] + g[k];
-            if (x0 + e < nx)
-                gm.v[e] -= a.wi2c_d * ((double)M[0] * Pm[0] + (double)M[1] * Pm[1] + (double)M[2] * Pm[2] +
-                                       (double)M[3] * Pm[3]);
-        }
-
-        // pushes: a^n_q(x - e_q) = h_q(x); what would leave the domain is
-        // handled by the edge rules below
-        const bool full = act && x0 + VEC <= nx;
-        const bool ylo = (y == 0), yhi = (y == ny - 1);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            // q = 1 to row y - 1 and q = 3 to row y + 1, inside the domain
-            if (act) {
-                S *d1 = aout + (1 * 6 + k) * plane + row - pitch;
-                S *d3 = aout + (3 * 6 + k) * plane + row + pitch;
-                if (full) {
-                    PK o1, o3;
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        o1.v[e] = to_store<S>(h[1][k][e]);
-                        o3.v[e] = to_store<S>(h[3][k][e]);
-                    }
-                    if (!ylo) *reinterpret_cast<PK *>(d1) = o1;
-                    if (!yhi) *reinterpret_cast<PK *>(d3) = o3;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if (x0 + e < nx) {
-                            if (!ylo) d1[e] = to_store<S>(h[1][k][e]);
-                            if (!yhi) d3[e] = to_store<S>(h[3][k][e]);
-                        }
-                }
-            }
-            // q = 0 to column x - 1: position p = x0 + e takes h_0(p + 1), p <= nx - 2
-            {
-                const T nxt = __shfl_down_sync(FULL_MASK, h[0][k][0], 1);
-                S *d0 = aout + (0 * 6 + k) * plane + row;
-                bool all = true;
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) all = all && (x0 + e <= nx - 2) && !(lane == 31 && e == VEC - 1);
-                if (all) {
-                    PK o;
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) o.v[e] = to_store<S>(e < VEC - 1 ? h[0][k][e + 1] : nxt);
-                    *reinterpret_cast<PK *>(d0) = o;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if (x0 + e <= nx - 2 && !(lane == 31 && e == VEC - 1))
-                            d0[e] = to_store<S>(e < VEC - 1 ? h[0][k][e + 1] : nxt);
-                }
-                if (lane == 0 && act && x0 >= 1) d0[-1] = to_store<S>(h[0][k][0]);  // the previous segment's last position
-            }
-            // q = 2 to column x + 1: position p = x0 + e takes h_2(p - 1), 1 <= p <= nx - 1
-            {
-                const T prv = __shfl_up_sync(FULL_MASK, h[2][k][VEC - 1], 1);
-                S *d2 = aout + (2 * 6 + k) * plane + row;
-                bool all = true;
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) all = all && (x0 + e >= 1) && (x0 + e <= nx - 1) && !(lane == 0 && e == 0);
-                if (all) {
-                    PK o;
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) o.v[e] = to_store<S>(e == 0 ? prv : h[2][k][e - 1]);
-                    *reinterpret_cast<PK *>(d2) = o;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if (x0 + e >= 1 && x0 + e <= nx - 1 && !(lane == 0 && e == 0))
-                            d2[e] = to_store<S>(e == 0 ? prv : h[2][k][e - 1]);
-                }
-                if (lane == 31 && x0 + VEC <= nx - 1) d2[VEC] = to_store<S>(h[2][k][VEC - 1]);  // the next segment's first
-            }
-        }
-
-        // Edge rules, transposed (Eqs. 23-25), at the lane's boundary nodes.
-        // The node x_b pulled f_d(x_b) = D f*_{-d}(x_b) + S_d(U^n(x_b)) (or, on a
-        // periodic edge, the opposite node's f*_d), so its h_d goes to
-        // a^n_{-d}(x_b) with D (or back to that opposite node). A traction
-        // edge adds the implicit-function derivative of F^b, which reaches
-        // every q of x_b through U^n = sum_q f*^n_q: its F-part is left in
-        // tug_out for the next step to add, and its mu-part goes to dL/dmu.
-        // No other thread writes the cells written here.
-        if (act && (ylo || yhi || x0 == 0 || x0 + VEC >= nx)) {
-            T ug[VEC][4];
-            bool tr[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                tr[e] = false;
-#pragma unroll
-                for (int m = 0; m < 4; ++m) ug[e][m] = T(0);
-            }
-#pragma unroll
-            for (int ed = 0; ed < 4; ++ed) {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const int x = x0 + e;
-                    if (x >= nx) continue;
-                    const bool on = (ed == EDGE_LEFT) ? x == 0 : (ed == EDGE_RIGHT) ? x == nx - 1 : (ed == EDGE_BOTTOM) ? ylo : yhi;
-                    if (!on) continue;
-                    const int d = edge_dmiss(ed), md = edge_dout(ed);
-                    T hd[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) hd[k] = h[d][k][e];
-                    if (a.kind[ed] == BC_PERIODIC) {
-                        const int tx = (ed == EDGE_LEFT) ? nx - 1 : (ed == EDGE_RIGHT) ? 0 : x;
-                        const int ty = (ed == EDGE_BOTTOM) ? ny - 1 : (ed == EDGE_TOP) ? 0 : y;
-                        const long long cell = (long long)(ty + 1) * pitch + a.L.xoff + tx;
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) aout[(d * 6 + k) * plane + cell] = to_store<S>(hd[k]);
-                        continue;
-                    }
-                    const T sv = (a.kind[ed] == BC_VELOCITY) ? T(-1) : T(1);  // D on (v1, v2); -sv on F
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) aout[(md * 6 + k) * plane + row + e] = to_store<S>((k < 2 ? sv : -sv) * hd[k]);
-                    if (a.kind[ed] != BC_TRACTION) continue;
-                    tr[e] = true;
-                    // the forward stored ghost = -f*_{-d} + G^b / 2 on the F-components
-                    int gx, gy;
-                    ghost_cell(ed, (ed <= EDGE_RIGHT) ? y : x, nx, ny, gx, gy);
-                    const long long gcell = (long long)(gy + 1) * pitch + a.L.xoff + gx;
-                    T Gb[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        Gb[m] = T(2) * (ld_r(fin[(d * 6 + 2 + m) * plane + gcell]) + ld_r(fin[(md * 6 + 2 + m) * plane + row + e]));
-                    T dmu;
-                    traction_ift<LAW, T>(ed, Gb, hd, mu.v[e], a.lam_ratio, ug[e], dmu);
-                    gm.v[e] += (double)dmu;
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (tr[e])
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) a.tug_out[m * a.L.uplane + urow + e] = ug[e][m];
-        }
-        if (act) *reinterpret_cast<PD *>(a.gmu + urow) = gm;
+        adj_finish<S, LAW, VEC>(a, y, x0, lane, U, h, mu, ub0, ub1, gm);
     }
 }
 
@@ -550,16 +639,21 @@ constexpr int adj_vec()
     return sizeof(S) == 8 ? 2 : ADJ_VEC32;
 }
 
+template <typename S, int LAW>
+static cudaError_t launch_adj_t(const void *args, int grid, cudaStream_t st)
+{
+    using T = typename Prec<S>::R;
+    const auto &a = *static_cast<const AdjArgs<T> *>(args);
+    return launch_pdl(k_adj<S, LAW, adj_vec<S>()>, grid, 128, 0, st, a);
+}
+
 template <typename S>
 static cudaError_t launch_adj_s(int law, const void *args, int grid, cudaStream_t st)
 {
-    using T = typename Prec<S>::R;
-    constexpr int VEC = adj_vec<S>();
-    const auto &a = *static_cast<const AdjArgs<T> *>(args);
     switch (law) {
-    case LAW_SVK: return launch_pdl(k_adj<S, LAW_SVK, VEC>, grid, 128, 0, st, a);
-    case LAW_NH: return launch_pdl(k_adj<S, LAW_NH, VEC>, grid, 128, 0, st, a);
-    default: return launch_pdl(k_adj<S, LAW_LOGNH, VEC>, grid, 128, 0, st, a);
+    case LAW_SVK: return launch_adj_t<S, LAW_SVK>(args, grid, st);
+    case LAW_NH: return launch_adj_t<S, LAW_NH>(args, grid, st);
+    default: return launch_adj_t<S, LAW_LOGNH>(args, grid, st);
     }
 }
 

@@ -183,7 +183,9 @@ __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> 
 
 // FP64 and FP32 storage: VEC nodes per lane as 16-byte vectors, unpacked.
 // One (row, segment) task of lattice `a`, executed by a whole warp.
-template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
+// NOQ: no displacement quadrature (states recomputed only for their
+// populations, as the adjoint's checkpoint segments are).
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false>
 __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a, int task, int lane,
                                           unsigned &flags)
 {
@@ -273,13 +275,15 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
                     }
                 }
             // Eq. (22): u*^{n+1} = u*^n + dt v^n (the two half steps of the paper)
-            const long long urow = (long long)y * a.L.upitch + x0;
+            if constexpr (!NOQ) {
+                const long long urow = (long long)y * a.L.upitch + x0;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                PD u = *reinterpret_cast<const PD *>(a.ustar + c * a.L.uplane + urow);
+                for (int c = 0; c < 2; ++c) {
+                    PD u = *reinterpret_cast<const PD *>(a.ustar + c * a.L.uplane + urow);
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) u.v[e] += a.dt * (double)vel[c][e];
-                *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
+                    for (int e = 0; e < VEC; ++e) u.v[e] += a.dt * (double)vel[c][e];
+                    *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
+                }
             }
             if (FUSE) lane_ghosts<LAW, S, VEC, MATF>(a, fout, row, x0, y, flags);
         }

@@ -9,7 +9,7 @@
 #include "lbm_launch.cuh"
 
 namespace tlv {
-template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false>
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
 {
     pdl_enter();
@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
     unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF>(a, task, lane, flags);
+    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
@@ -98,9 +98,15 @@ static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fu
         if constexpr (LAW > LAW_LOGNH) {
             return cudaErrorNotSupported;
         } else if constexpr (sizeof(S) == 2) {
+            if (!a.ustar) return cudaErrorInvalidValue;
             return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, true>, grid, 128, 0, st, a)
                         : launch_pdl(k_step16<S, LAW, STEP16_V, false, true>, grid, 128, 0, st, a);
         } else {
+            // without u*: a step recomputed only for its populations (the
+            // adjoint's checkpoint segments), 32 bytes per node less
+            if (!a.ustar)
+                return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true, true>, grid, 128, 0, st, a)
+                            : launch_pdl(k_step<S, LAW, VEC, false, true, true>, grid, 128, 0, st, a);
             return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true>, grid, 128, 0, st, a)
                         : launch_pdl(k_step<S, LAW, VEC, false, true>, grid, 128, 0, st, a);
         }

@@ -1,7 +1,7 @@
 """Per-node material fields and the adjoint through the C ABI.
 
 Forward with a shear-modulus field against the FP64 oracle (every storage
-type; the 16-bit formats with test_gpu_parity's 4 * 2^-p * sqrt(n) bound); the GPU
+type, with test_gpu_parity's bounds); the GPU
 gradients (FP64 and FP32 storage) against the oracle's reference adjoint on
 lattices that span several warp segments with a ragged tail; independence of
 the checkpoint interval (recomputed segments are bit-identical); central
@@ -13,9 +13,10 @@ Tolerances. FP64 storage: the gradients are sums over the run of products
 of quantities each within about 1e-12 (relative) of the oracle's; 1e-9
 relative L2 per gradient field leaves three orders of magnitude for their
 accumulation. FP32 storage: the adjoint recursion is linear in the forward
-state, whose per-group FP32 bound is 1e-4 (tests/test_gpu_parity.py), and
-the adjoint itself is computed in FP32 with the same rounding per step, so
-the gradient fields get the same 1e-4 relative L2."""
+state, whose per-group FP32 bound is 1e-5 (tests/test_gpu_parity.py), and
+the adjoint itself is computed in FP32 with the same rounding per step and
+sums those products over the run; the gradient fields get 1e-4 relative L2
+(measured: 7e-6 for mu, 6e-6 for v0)."""
 import numpy as np
 import pytest
 
@@ -131,10 +132,11 @@ def test_material_field_forward_matches_oracle(lbm, storage):
     O.step(w.steps)
     Uo, Po, So = O.state()
     errs = group_errors({"U": U, "P": P, "u": u, "sigma": So}, {"U": Uo, "P": Po, "u": O.displacement(), "sigma": So})
-    tol = tol_for(storage, w.steps)
-    for k in ("v", "F-I", "P", "u"):
-        assert errs[k] <= tol["group"], (k, errs)
-    assert errs["U"] <= tol["U"], errs
+    print("ADJFWD storage=%d" % storage, {k: "%.2e" % v for k, v in errs.items()})
+    tol = tol_for(storage, w.steps, {"U": Uo, "P": Po}, w.c,
+                  (w.params["lam_ratio"] + 2.0) * float(np.max(w.params["mu"])))
+    for k in ("v", "F-I", "P", "u", "U"):
+        assert errs[k] <= tol[k], (k, errs)
 
 
 @pytest.mark.parametrize("storage", [F64, F32])
