@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
         // step-0 collision (Eqs. 10, 12, 14) on the offsets from the rest
         // state, which the collision leaves fixed
         R Un[6], dJ;
+#pragma unroll
         for (int k = 0; k < 6; ++k) Un[k] = (f[0][k] + f[2][k]) + (f[1][k] + f[3][k]);
         Un[0] += (R)(0.5 * dt * a.b1);
         Un[1] += (R)(0.5 * dt * a.b2);
@@ -37,12 +38,15 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
         piola_any_t<R>(a.m.law, Gn, m, Pn, dJ);
         feq_ofs<R>(Un, Pn, c, feq);
         const R src[2] = {(R)(dt * (2.0 - a.omega) * 0.125 * a.b1), (R)(dt * (2.0 - a.omega) * 0.125 * a.b2)};
+#pragma unroll
         for (int q = 0; q < 4; ++q)
+#pragma unroll
             for (int k = 0; k < 6; ++k) {
                 R fs = f[q][k] + w * (feq[q][k] - f[q][k]);
                 if (k < 2) fs += src[k];
                 fout[pidx(a.L, q, k, x, y)] = to_store<T>(fs);
             }
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
             const double u0 = a.u0 ? a.u0[k * N + n] : 0.0;
             a.ustar[k * a.L.uplane + (long long)y * a.L.upitch + x] =

@@ -38,7 +38,9 @@ __device__ __forceinline__ void feq_ofs(const R U[6], const R P[4], R c, R feq[4
     const R PhiX[6] = {-P[0], -P[2], -U[0], R(0), -U[1], R(0)};
     const R PhiY[6] = {-P[1], -P[3], R(0), -U[0], R(0), -U[1]};
     const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
+#pragma unroll
     for (int q = 0; q < 4; ++q)
+#pragma unroll
         for (int k = 0; k < 6; ++k) feq[q][k] = R(0.25) * (U[k] + (R(2) / c) * (ci[q] * PhiX[k] + cj[q] * PhiY[k]));
 }
 
@@ -54,6 +56,7 @@ __device__ inline bool init_node_ofs(const InitArgs &a, int x, int y, const LawP
     const int ci[4] = {1, 0, -1, 0}, cj[4] = {0, 1, 0, -1};
     const R c = (R)a.c, dt = (R)a.dt;
     R U[6];  // U0 - U_rest
+#pragma unroll
     for (int k = 0; k < 6; ++k) U[k] = (R)(a.U0[k * N + n] - ((k == 2 || k == 5) ? 1.0 : 0.0));
     const R G[4] = {U[2], U[3], U[4], U[5]};
     const R F[4] = {R(1) + U[2], U[3], U[4], R(1) + U[5]};
@@ -63,6 +66,7 @@ __device__ inline bool init_node_ofs(const InitArgs &a, int x, int y, const LawP
     if (a.order == 2) {
         R gX[6], gY[6], dPX[4], dPY[4];
         const double h = 0.5 / a.dx;
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
             gX[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 0, a.xper, h);
             gY[k] = (R)fd(a.U0 + k * N, nx, ny, x, y, 1, a.yper, h);
@@ -70,6 +74,7 @@ __device__ inline bool init_node_ofs(const InitArgs &a, int x, int y, const LawP
         // d_alpha P = C : d_alpha F (text after Eq. 18), as Jacobian actions (Eq. 8)
         tangent_jvp_t<R>(a.m.law, F, gX + 2, m, dPX);
         tangent_jvp_t<R>(a.m.law, F, gY + 2, m, dPY);
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
             const R i = (R)ci[q], j = (R)cj[q];
             R Z[6], dP[4];
@@ -88,6 +93,7 @@ __device__ inline bool init_node_ofs(const InitArgs &a, int x, int y, const LawP
                              R(0.25) * (Z[3] - (R(2) * j / c) * Z[0]),
                              R(0.25) * (Z[4] - (R(2) * i / c) * Z[1]),
                              R(0.25) * (Z[5] - (R(2) * j / c) * Z[1])};
+#pragma unroll
             for (int k = 0; k < 6; ++k) f[q][k] -= R(0.5) * dt * Dq[k];
         }
     }

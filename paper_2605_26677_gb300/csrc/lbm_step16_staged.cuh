@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(128, Stage16<NS>::MIN_BLOCKS) k_step16s(const 
 
 // Which 16-bit step kernel runs: LBM_STEP16 in the environment when set
 // (step16_env_choice), else the context's own choice (StepArgs::k16), which
-// lbm_init makes by timing both on the lattice. The register kernel is the
-// faster one on most lattices measured (BF16 us per step, register / staged:
-// 2896^2 periodic 187.0 / 194.4, 8192^2 periodic 1391.5 / 1591.8), the staged
-// one on some (4096 x 2048 clamped 192.3 / 185.0).
+// the first lbm_step makes by timing both on the lattice. The register
+// kernel is the faster one on most lattices measured (BF16 us per step,
+// register / staged: 2048^2 periodic 98.9 / 105.4, 8192^2 periodic 1405 /
+// 1586), the staged one on some (4096 x 2048 clamped 190.5 / 187.0).
 static int step16_stages(int ctx_choice)
 {
     const int e = step16_env_choice();

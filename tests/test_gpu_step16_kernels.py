@@ -3,10 +3,10 @@
 shared memory by bulk asynchronous copies; LBM_STEP16=staged) run the same
 tasks through the same per-node arithmetic, so after any number of steps
 their states, displacements and diagnostics agree bit for bit; so does the
-default, where lbm_init times both kernels on the lattice with trial steps
-that must leave the state untouched, and keeps the faster. The choice is
-read once per process, so each variant runs in a child process over the
-same cases; agreement with the oracle is the 16-bit part of
+default, where the first lbm_step times both kernels on the lattice with
+trial steps that must leave the state untouched, and keeps the faster. The
+choice is read once per process, so each variant runs in a child process
+over the same cases; agreement with the oracle is the 16-bit part of
 test_gpu_parity, which runs the default.
 
 Cases: ragged widths (1000 = 7 segments of 128 and a tail of 104; 131 = one
