@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--form", choices=["batch", "adjoint", "bf16"], default=None,
                    help="run only this side measurement and print its JSON (profiling); not a bench line")
     p.add_argument("--form-steps", type=int, default=None, help="steps of the --form run")
+    p.add_argument("--batch-members", type=int, default=None,
+                   help="--form batch with only the first so many specimens (profiling)")
     p.add_argument("--size", type=int, default=8192,
                    help="side of the periodic square (profiling of smaller cases; the workload is 8192)")
     return p.parse_args()
@@ -410,13 +412,16 @@ def workload_config(wp, ws, bpn):
             "l2": "inputs larger than L2 (%.1f GB moved per step)" % (bpn * N / 1e9)}
 
 
-def batch_form(lbm, torch, peak, steps, graph_steps=20):
+def batch_form(lbm, torch, peak, steps, graph_steps=20, members=None):
     """256 specimens of uneven size and material (FP32) advanced by the
     batched launches: tuned tiles replayed from a CUDA graph (the value), and
-    beside it the same with direct launches and with the default tiles."""
+    beside it the same with direct launches and with the default tiles.
+    members: only the first so many specimens (profiling of a smaller case)."""
     from synth.generators import specimen_batch
 
     ws = specimen_batch()
+    if members:
+        ws = ws[:members]
     kinds = {"velocity": lbm.LBM_BC_VELOCITY, "traction": lbm.LBM_BC_TRACTION}
     Ls = []
     for w in ws:
@@ -608,7 +613,8 @@ def main():
         from paper_2605_26677_gb300 import lbm
 
         if args.form == "batch":
-            line = {"form": "batch", **batch_form(lbm, torch, peaks()[0], args.form_steps or 200)}
+            line = {"form": "batch", **batch_form(lbm, torch, peaks()[0], args.form_steps or 200,
+                                                  members=args.batch_members)}
         elif args.form == "bf16":
             from synth import clamped_specimen
 

@@ -149,9 +149,15 @@ __device__ __forceinline__ void adj_finish(const AdjArgs<typename Prec<S>::R> &a
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 6; ++k) h[q][k][e] = a.one_m_omega * h[q][k][e] + g[k];
-        if (x0 + e < nx)
-            gm.v[e] -= a.wi2c_d * ((double)M[0] * Pm[0] + (double)M[1] * Pm[1] + (double)M[2] * Pm[2] +
-                                   (double)M[3] * Pm[3]);
+        // the step's dL/dmu term is formed in the compute type and only
+        // accumulated over the run in FP64 (on GB300 FP64 instructions are
+        // scarce: forming it in FP64 kept the FP64 pipe 42% busy)
+        if (x0 + e < nx) {
+            if constexpr (sizeof(T) == 4)
+                gm.v[e] -= (double)(a.wi2c * (M[0] * Pm[0] + M[1] * Pm[1] + M[2] * Pm[2] + M[3] * Pm[3]));
+            else
+                gm.v[e] -= a.wi2c_d * (M[0] * Pm[0] + M[1] * Pm[1] + M[2] * Pm[2] + M[3] * Pm[3]);
+        }
     }
 
     // pushes: a^n_q(x - e_q) = h_q(x); what would leave the domain is
