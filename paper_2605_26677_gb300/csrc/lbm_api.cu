@@ -239,10 +239,36 @@ lbm_status read_device(lbm_ctx *c, double *U, double *P, double *sigma, double *
     return LBM_OK;
 }
 
-// run fn(device buffer) then copy `count` doubles to host `dst`
+// Device-visible address of a host array that the context's GPU can write
+// in place, or nullptr: page-locked memory (cudaHostAlloc, cudaHostRegister)
+// allocated for that device, which a GB300 reaches over NVLink-C2C at about
+// the rate of a copy. The read-out kernels then write the caller's array
+// directly: no device staging buffer and no separate copy (8192^2: the state
+// read-out 30 -> 17 ms, the displacement 10.5 -> 5.6 ms). Pageable memory
+// takes the copy path. The initialization keeps its copy: its stencil reads
+// each input value several times, and read in place over NVLink-C2C it took
+// 48 ms against 35 ms copied.
+static void *host_alias(const lbm_ctx *c, const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer && at.device == c->cfg.device) return at.devicePointer;
+    return nullptr;
+}
+
+// run fn(device buffer) then copy `count` doubles to host `dst`; a
+// page-locked dst is written by fn in place
 template <typename Fn>
 lbm_status read_to_host(lbm_ctx *c, double *dst, size_t count, Fn fn)
 {
+    if (double *alias = static_cast<double *>(host_alias(c, dst))) {
+        lbm_status s = fn(alias);
+        if (s != LBM_OK) return s;
+        return sync_status(c);
+    }
     double *tmp = nullptr;
     CK(c, cudaMallocAsync((void **)&tmp, count * sizeof(double), c->st));
     lbm_status s = fn(tmp);

@@ -234,3 +234,40 @@ def test_rest_state_is_exact_on_gpu(lbm):
         U, P, _ = lbm.lbm_read_state(L.ctx)
         assert np.array_equal(U, rest(nx, ny)) and not P.any()
         L.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_page_locked_host_arrays_give_the_same_results(lbm, storage):
+    """Page-locked host arrays are written in place by the read-out kernels;
+    pageable ones go through a device copy. Both routes give the same bits
+    (and page-locked inputs to lbm_init the same state as pageable ones)."""
+    import torch
+
+    nx, ny = 150, 37
+    U0 = smooth_field(nx, ny, seed=9, amp=0.04, periodic=False)
+    u0 = 0.01 * smooth_field(nx, ny, seed=10)[:2]
+    res = []
+    for pinned in (False, True):
+        L = make(lbm, nx, ny, storage=storage, omega=1.9)
+        lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+        lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.01))
+        if pinned:
+            a = torch.from_numpy(U0).pin_memory().numpy()
+            b = torch.from_numpy(u0).pin_memory().numpy()
+            Uo = torch.full((6, ny, nx), np.nan, dtype=torch.float64).pin_memory().numpy()
+            Po = torch.full((4, ny, nx), np.nan, dtype=torch.float64).pin_memory().numpy()
+            uo = torch.full((2, ny, nx), np.nan, dtype=torch.float64).pin_memory().numpy()
+            so = torch.full((4, ny, nx), np.nan, dtype=torch.float64).pin_memory().numpy()
+        else:
+            a, b = U0.copy(), u0.copy()
+            Uo, Po, uo, so = (np.full((m, ny, nx), np.nan) for m in (6, 4, 2, 4))
+        lbm.lbm_init(L.ctx, a, b, 2)
+        lbm.lbm_step(L.ctx, 25)
+        lbm.lbm_read_state(L.ctx, Uo, Po)
+        lbm.lbm_read_displacement(L.ctx, uo)
+        lbm.lbm_read_cauchy(L.ctx, so)
+        res.append([np.array(x, copy=True) for x in (Uo, Po, uo, so)])
+        L.close()
+    for x, y in zip(*res):
+        assert np.all(np.isfinite(x))
+        assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
