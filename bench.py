@@ -201,7 +201,7 @@ def timed_steps(lbm, torch, L, steps, warmup, dist, census_steps=10):
     (ns, ts), (ne, te) = prof["step"], prof["edges"]
     share = ts / (ts + te) if ts + te > 0 else 1.0
     info = {"launches_per_step": (ns + ne) / census_steps, "step_kernel_ms": ms / steps * share,
-            "edge_kernel_ms": te / max(ne, 1)}
+            "edge_kernel_ms": te / max(ne, 1), "step_variant": lbm.lbm_step_variant(L.ctx)}
     return ms, info
 
 
@@ -325,7 +325,7 @@ def run_ours(args, rank, ws, dist):
             gbs = b8 * N / (i8["step_kernel_ms"] * 1e-3) / 1e9
             forms[name + "_periodic_8192x8192"] = {
                 "value": N * k / (ms8 * 1e-3) / 1e6, "unit": UNIT, "steps": k, "kernel_GBs": gbs,
-                "roofline_frac": gbs / peak, "bytes_per_node": b8,
+                "roofline_frac": gbs / peak, "bytes_per_node": b8, "step_variant": i8["step_variant"],
                 "note": "16-mode random velocity field, NH lambda=1.5 mu=0.75, omega=2; populations stored as "
                         "%s offsets from the rest equilibrium, FP32 compute, FP64 u*" % name}
         del Up, up
@@ -341,6 +341,7 @@ def run_ours(args, rank, ws, dist):
         forms["fp32_clamped_specimen_4096x2048"] = {
             "value": Nc * k / (msc * 1e-3) / 1e6, "unit": UNIT, "steps": k, "kernel_GBs": gbs,
             "roofline_frac": gbs / peak, "bytes_per_node": bc, "traffic_bytes_per_node": tc,
+            "step_variant": ic["step_variant"],
             "note": "clamped left, traction-free top and bottom, traction ramp 0.3 mu on the right, NH lambda=2 "
                     "mu=1, body force 1e-6, c=5, omega=1.95; edge rules fused into the step kernel"}
         L = setup_ctx(lbm, w, lbm.LBM_STORE_F64, U0, u0)
@@ -350,6 +351,7 @@ def run_ours(args, rank, ws, dist):
         forms["fp64_clamped_specimen_4096x2048"] = {
             "value": Nc * k / (ms64 * 1e-3) / 1e6, "unit": UNIT, "steps": k,
             "kernel_GBs": b64 * Nc / (i64["step_kernel_ms"] * 1e-3) / 1e9, "bytes_per_node": b64,
+            "step_variant": i64["step_variant"],
             "note": "FP64 populations (parity mode); FP64 ALU-bound on GB300"}
         fp64 = recorded_fp64_counts()
         if fp64 is not None:
@@ -367,7 +369,7 @@ def run_ours(args, rank, ws, dist):
             gbs = bh * Nc / (ih["step_kernel_ms"] * 1e-3) / 1e9
             forms[name + "_clamped_specimen_4096x2048"] = {
                 "value": Nc * k / (msh * 1e-3) / 1e6, "unit": UNIT, "steps": k, "kernel_GBs": gbs,
-                "roofline_frac": gbs / peak, "bytes_per_node": bh,
+                "roofline_frac": gbs / peak, "bytes_per_node": bh, "step_variant": ih["step_variant"],
                 "note": "populations stored as %s offsets from the rest equilibrium, FP32 compute, FP64 u*" % name}
         del U0, u0
 
@@ -388,7 +390,7 @@ def run_ours(args, rank, ws, dist):
                      "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                      "traffic": None if traffic_bpn is None else traffic_bpn * N,
                      "kernel": "k_step (fused pull-stream + collide + quadrature)",
-                     "bytes_per_node_update": bpn, "launch_ms": kern_ms,
+                     "bytes_per_node_update": bpn, "launch_ms": kern_ms, "step_variant": tinfo["step_variant"],
                      "edge_kernel_ms": tinfo["edge_kernel_ms"],
                      "launch_ms_source": "CUDA events around the timed region / launches (no per-launch events in it)"},
         "e2e": {"value": round(e2e, 1), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
@@ -450,6 +452,7 @@ def batch_form(lbm, torch, peak, steps, graph_steps=20, members=None):
     default_tiles = lbm.lbm_batch_get_tiles(b)
     ms_default = run(graph_steps)
     tiles, us = lbm.lbm_batch_tune(b, reps=10)
+    orders = lbm.lbm_batch_get_task_orders(b)
     ms = run(graph_steps)
     ms_direct = run(0)
     info = lbm.lbm_batch_info(b)
@@ -460,7 +463,7 @@ def batch_form(lbm, torch, peak, steps, graph_steps=20, members=None):
     return {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps, "kernel_GBs": gbs,
             "roofline_frac": gbs / peak, "bytes_per_node": bpn, "nodes": nodes,
             "launches_per_step": info["launches_per_step"], "graph_steps": graph_steps,
-            "tiles": tiles, "default_tiles": default_tiles,
+            "tiles": tiles, "task_orders_dynamic": orders, "default_tiles": default_tiles,
             "tune_us": [[round(x, 1) for x in row] for row in us.tolist()],
             "value_direct_launches": nodes * steps / (ms_direct * 1e-3) / 1e6,
             "value_default_tiles": nodes * steps / (ms_default * 1e-3) / 1e6,
@@ -625,7 +628,7 @@ def main():
             ms, ti = timed_steps(lbm, torch, L, k, 5, None)
             L.close()
             line = {"form": "bf16", "value": w.nx * w.ny * k / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": k,
-                    "kernel_us": ti["step_kernel_ms"] * 1e3}
+                    "kernel_us": ti["step_kernel_ms"] * 1e3, "step_variant": ti["step_variant"]}
         else:
             line = {"form": "adjoint", **adjoint_form(lbm, torch, args.form_steps or 2000, all_states=False)}
     elif args.impl == "reference":

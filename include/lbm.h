@@ -36,8 +36,8 @@
  *     converge, a non-finite state) are latched in a device status word; the
  *     next call that synchronises (lbm_step, lbm_sync, lbm_read_*) returns the
  *     matching LBM_ERR_* code. The state stays readable after such an error.
- *     lbm_init clears the latch. The staged 16-bit step kernel (selected by
- *     LBM_STEP16=staged in the environment) bounds each wait for its
+ *     lbm_init clears the latch. The staged 16-bit step kernel (chosen by
+ *     the first lbm_step, see there) bounds each wait for its
  *     asynchronous copies to one second; one that runs out is latched the
  *     same way and returned as LBM_ERR_CUDA, and the steps that followed it
  *     are not valid.
@@ -195,18 +195,26 @@ lbm_status lbm_init(lbm_ctx *ctx, const double *U0, const double *u0, int32_t or
 lbm_status lbm_init_device(lbm_ctx *ctx, const double *U0_dev, const double *u0_dev, int32_t order);
 
 /* Advance nsteps >= 0 time steps (Sec. 3.7), then wait and return the
- * latched device status. With BF16 or FP16 storage (and the node form of
- * F^b) the first call with nsteps > 0 after lbm_init or lbm_init_device
- * first times the library's two 16-bit step kernels, which give identical
- * results, with a few trial steps that leave the state untouched, and keeps
- * the faster for this context (the trials take a u*-sized scratch
- * allocation while they run). Until then, and for lbm_step_async, the
- * register kernel runs. LBM_STEP16=regs or LBM_STEP16=staged in the
- * environment skips the trials and forces that kernel. */
+ * latched device status. With uniform material and the node form of F^b,
+ * the context's first call with nsteps > 0 (after its first lbm_init or
+ * lbm_init_device) first times the step-launch variants, which give
+ * identical results: the task order (static, or claimed dynamically from a
+ * device counter) and, with BF16 or FP16 storage, the register or the
+ * shared-memory staged kernel; a few trial steps leave the state untouched,
+ * and the fastest is kept for the context's life (the trials take a
+ * u*-sized scratch allocation while they run). Until then, and for
+ * lbm_step_async, the register kernel runs in static order. LBM_STEP16=regs
+ * or staged and LBM_DYN=0 or 1 in the environment restrict the choice. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* As lbm_step without waiting; check later with lbm_sync. */
 lbm_status lbm_step_async(lbm_ctx *ctx, int64_t nsteps);
+
+/* The step-launch variant the context runs now (host outputs, either may be
+ * NULL): *staged = 1 for the shared-memory staged 16-bit kernel, 0 for the
+ * register kernel; *dynamic = 1 for dynamic task order, 0 for static. No
+ * device work. */
+lbm_status lbm_step_variant(const lbm_ctx *ctx, int32_t *staged, int32_t *dynamic);
 
 /* Wait for the context's stream and return the latched device status. */
 lbm_status lbm_sync(lbm_ctx *ctx);
@@ -292,7 +300,10 @@ lbm_status lbm_diagnostics_state_noalloc(const double *U_dev, int32_t nx, int32_
  * Tiles that exist: F64 {1, 2}, F32 {1, 2, 4}, BF16 / F16 {2, 4}. The default
  * tile of a class is the widest whose segment is no wider than the class's
  * largest nx (48, 96, 192, 384; the narrowest if none is); lbm_batch_tune
- * measures them all.
+ * measures them all. The tasks of a group are taken in static order (warp w
+ * of W takes tasks w, w + W, ...) or, per size class, in dynamic order
+ * (warps claim the next task from a device counter, so that warps slowed by
+ * short or edge tasks take fewer); the order changes no result.
  *
  * The batch owns a stream of its own. Every call orders its device work after
  * the work already enqueued on the members' streams, and the members' streams
@@ -320,13 +331,20 @@ int32_t lbm_batch_size_class(int32_t nx);
 lbm_status lbm_batch_get_tiles(const lbm_batch *b, int32_t *vec);
 lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t size_class, int32_t vec);
 
+/* Task order of the size classes: dynamic[LBM_BATCH_CLASSES] (host), 0 static
+ * (the default), 1 dynamic. lbm_batch_set_task_order returns LBM_ERR_ARG for
+ * a class out of range or a value other than 0 or 1. */
+lbm_status lbm_batch_get_task_orders(const lbm_batch *b, int32_t *dynamic);
+lbm_status lbm_batch_set_task_order(lbm_batch *b, int32_t size_class, int32_t dynamic);
+
 /* Autotuner: for every size class that has members, times `reps` (>= 1)
- * launches of that class alone for each tile that exists and keeps the
- * fastest. The trial launches write only the members' second population
- * buffer and scratch copies of the displacement accumulator and status, so
- * the members' states do not change. us (host, optional) receives
- * LBM_BATCH_CLASSES x 3 doubles: mean microseconds per launch for the tiles
- * in the order listed above (0 where not tried). Synchronises. */
+ * launches of that class alone for each tile that exists, in each task order,
+ * and keeps the fastest (tile, order). The trial launches write only the
+ * members' second population buffer and scratch copies of the displacement
+ * accumulator and status, so the members' states do not change. us (host,
+ * optional) receives LBM_BATCH_CLASSES x 3 doubles: mean microseconds per
+ * launch for the tiles in the order listed above, the faster of the two task
+ * orders (0 where not tried). Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us);
 
 /* Advance every member by nsteps >= 0 steps. graph_steps = 0 enqueues the

@@ -146,6 +146,10 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     }
     a.gdev = nullptr;
     a.k16 = c->k16;
+    a.ctr2 = c->dyn ? c->d_ctr : nullptr;
+    a.ctr_par = const_cast<int *>(&c->ctr_par);  // advanced by the launcher of each dynamic launch
+    a.ctr = nullptr;
+    a.ctr_next = nullptr;
     return a;
 }
 
@@ -500,6 +504,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     CKC(cudaMalloc((void **)&c->ustar, ubytes));
     CKC(cudaMalloc((void **)&c->d_status, sizeof(int)));
     CKC(cudaMalloc((void **)&c->d_diag, (size_t)(diag_blocks(c->L) * 10 + 10) * sizeof(double)));
+    CKC(cudaMalloc((void **)&c->d_ctr, 2 * sizeof(unsigned)));
+    CKC(cudaMemset(c->d_ctr, 0, 2 * sizeof(unsigned)));
+    c->dyn = tlv::dyn_env_choice() == 1;  // until the first lbm_step chooses
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->ustar, 0, ubytes, c->st));
@@ -524,6 +531,7 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->ustar);
     cudaFree(c->d_status);
     cudaFree(c->d_diag);
+    cudaFree(c->d_ctr);
     for (int e = 0; e < 4; ++e) cudaFree(c->d_profile[e]);
     cudaFree(c->d_mufield);
     cudaFree(c->d_muplane);
@@ -714,32 +722,62 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     c->step = 0;
     c->initialized = true;
     c->ghosts_dirty = true;
-    c->k16_pending = true;
     return LBM_OK;
 }
 
-// The two 16-bit step kernels (registers; rows staged in shared memory)
-// produce bit-identical states, and which is faster depends on the lattice:
-// the first lbm_step after an initialization times both on this one and
-// keeps the faster. The trials read the current
-// buffer, whose ghost cells are refreshed first exactly as the first step
-// would, and write only the other buffer, which the first real step
-// overwrites; u* and the status word go to scratch, so the state is untouched.
-// Skipped when LBM_STEP16 forces a kernel, for the extrapolated F^b form,
-// with a material field (the register kernel carries it), or when the
-// scratch cannot be allocated (the register kernel then runs).
-static lbm_status tune_step16(lbm_ctx *c)
+// Step-launch variants: which 16-bit kernel (registers, or rows staged in
+// shared memory) and which task order (static grid-stride, or dynamic claims
+// from a device counter). All give bit-identical states, and which is
+// fastest depends on the lattice (BF16, fraction of the copy bandwidth:
+// 4096 x 2048 clamped register static 0.838, register dynamic 0.907, staged
+// 0.852; 8192^2 periodic 0.909, 0.709, 0.81; FP32 4096 x 2048 clamped static
+// 0.954, dynamic 0.934; 8192^2 periodic 0.954, 0.958). The first lbm_step of a
+// context times the candidates on its lattice and keeps the fastest for the
+// context's life. The trials read the current buffer, whose ghost cells are
+// refreshed first exactly as the first step would, and write only the other
+// buffer, which the first real step overwrites; u* and the status word go to
+// scratch, so the state is untouched. LBM_STEP16 and LBM_DYN in the
+// environment restrict the candidates; contexts with a material field or the
+// extrapolated F^b form, or without room for the scratch, keep the register
+// kernel in static order.
+} // extern "C"
+
+namespace {
+
+struct StepVariant {
+    int k16;
+    bool dyn;
+};
+
+template <typename T>
+lbm_status tune_step(lbm_ctx *c)
 {
-    if (c->eb != 2 || c->cfg.fb_mode != LBM_FB_NODE || c->d_muplane || tlv::step16_env_choice() >= 0) return LBM_OK;
+    if (c->cfg.fb_mode != LBM_FB_NODE || c->d_muplane) return LBM_OK;
+    std::vector<StepVariant> cand;
+    const int env16 = tlv::step16_env_choice(), envdyn = tlv::dyn_env_choice();
+    for (int k16 = 0; k16 < (c->eb == 2 ? 2 : 1); ++k16)
+        for (int d = 0; d < 2; ++d) {
+            if ((env16 >= 0 && k16 != env16) || (envdyn >= 0 && d != envdyn) || (k16 == 1 && d == 1)) continue;
+            cand.push_back({k16, d == 1});
+        }
+    if (cand.size() == 1) {
+        c->k16 = cand[0].k16;
+        c->dyn = cand[0].dyn;
+    }
+    if (cand.size() <= 1) return LBM_OK;
     if (c->ghosts_dirty) {
-        lbm_status s = refresh_ghosts<float>(c);
+        // the refresh the first step would make, timed like it when profiling
+        const bool prof = c->prof && (c->ev_step.size() < 200000);
+        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
+        lbm_status s = refresh_ghosts<T>(c);
         if (s != LBM_OK) return s;
+        if (prof && record(c, c->ev_edge) != LBM_OK) return LBM_ERR_CUDA;
     }
     double *us = nullptr;
     int *st = nullptr;
     const size_t ubytes = (size_t)2 * c->L.uplane * sizeof(double);
     if (cudaMallocAsync((void **)&us, ubytes, c->st) != cudaSuccess) {
-        cudaGetLastError();  // clear it: without scratch the register kernel runs
+        cudaGetLastError();  // clear it: without scratch the default variant runs
         return LBM_OK;
     }
     if (cudaMallocAsync((void **)&st, sizeof(int), c->st) != cudaSuccess) {
@@ -752,20 +790,24 @@ static lbm_status tune_step16(lbm_ctx *c)
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), c->st);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-    StepArgs<float> a = step_args<float>(c, c->cur);
+    StepArgs<T> a = step_args<T>(c, c->cur);
     a.ustar = us;
     a.status = st;
+    auto set = [&](const StepVariant &v) {
+        a.k16 = v.k16;
+        a.ctr2 = v.dyn ? c->d_ctr : nullptr;
+    };
     // a warm-up step of each, then three rounds of three steps of each
-    // kernel, interleaved so that clock changes weigh on both alike
-    constexpr int NK = 2;
-    float ms[NK] = {0.f, 0.f};
-    for (int v = 0; v < NK && e == cudaSuccess; ++v) {
-        a.k16 = v;
+    // variant, interleaved so that clock changes weigh on all alike
+    const int nk = (int)cand.size();
+    std::vector<float> ms(nk, 0.f);
+    for (int v = 0; v < nk && e == cudaSuccess; ++v) {
+        set(cand[v]);
         e = launch_step(c->cfg.storage, c->m.law, true, &a, c->grid_step, c->st);
     }
     for (int round = 0; round < 3 && e == cudaSuccess; ++round)
-        for (int v = 0; v < NK && e == cudaSuccess; ++v) {
-            a.k16 = v;
+        for (int v = 0; v < nk && e == cudaSuccess; ++v) {
+            set(cand[v]);
             float t = 0.f;
             e = cudaEventRecord(ev[0], c->st);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r)
@@ -777,9 +819,10 @@ static lbm_status tune_step16(lbm_ctx *c)
         }
     if (e == cudaSuccess) {
         int best = 0;
-        for (int v = 1; v < NK; ++v)
+        for (int v = 1; v < nk; ++v)
             if (ms[v] < ms[best]) best = v;
-        c->k16 = best;
+        c->k16 = cand[best].k16;
+        c->dyn = cand[best].dyn;
     }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
@@ -788,6 +831,10 @@ static lbm_status tune_step16(lbm_ctx *c)
     CK(c, e);
     return LBM_OK;
 }
+
+} // namespace
+
+extern "C" {
 
 static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
 {
@@ -851,17 +898,25 @@ lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
 
 lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
 {
-    if (c && c->initialized && c->k16_pending && nsteps > 0) {
-        // the first synchronising step after an initialization picks the
-        // 16-bit step kernel for the lattice
+    if (c && c->initialized && c->tune_pending && nsteps > 0) {
+        // the context's first synchronising step picks the step-launch
+        // variant for the lattice (tune_step)
         lbm_status s = check_edges(c);
-        if (s == LBM_OK) s = tune_step16(c);
+        if (s == LBM_OK) s = (c->eb == 8) ? tune_step<double>(c) : tune_step<float>(c);
         if (s != LBM_OK) return s;
-        c->k16_pending = false;
+        c->tune_pending = false;
     }
     lbm_status s = lbm_step_async(c, nsteps);
     if (s != LBM_OK) return s;
     return sync_status(c);
+}
+
+lbm_status lbm_step_variant(const lbm_ctx *c, int32_t *staged, int32_t *dynamic)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (staged) *staged = c->k16;
+    if (dynamic) *dynamic = c->dyn ? 1 : 0;
+    return LBM_OK;
 }
 
 lbm_status lbm_sync(lbm_ctx *c)

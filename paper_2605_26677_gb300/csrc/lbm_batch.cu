@@ -6,7 +6,7 @@
 // streams so that they overlap):
 //   [k_batch_time]            edge time factors of the step, if any member
 //                             has a time-dependent edge
-//   k_batch / k_batch16 x G   one launch per group (closure, tile)
+//   k_batch / k_batch16 x G   one launch per group (closure, tile, task order)
 // Two StepArgs arrays live in device memory, one per step parity: parity 0
 // reads each member's current buffer, parity 1 the other one, so a captured
 // graph of an even number of steps is valid for every call, and each call
@@ -28,6 +28,7 @@ namespace {
 constexpr int NCLASS = LBM_BATCH_CLASSES;
 constexpr int CLASS_MAX_NX[NCLASS - 1] = {48, 96, 192, 384};
 constexpr int TIME_CHUNK = 1024;  // steps of edge time factors per upload
+constexpr int MAX_GROUPS = 64;    // (closure, tile, order) groups; 6 x 3 x 2 exist
 
 int size_class(int nx)
 {
@@ -62,12 +63,13 @@ const void *kernel_for(int storage, int law, int vec)
 
 struct Group {
     int law = 0, vec = 0;
+    bool dyn = false;          // dynamic task order
     int first = 0, count = 0;  // range of plan.order
     int ntask = 0, grid = 0;
     const void *fn = nullptr;
     bool operator==(const Group &o) const
     {
-        return law == o.law && vec == o.vec && first == o.first && count == o.count && ntask == o.ntask &&
+        return law == o.law && vec == o.vec && dyn == o.dyn && first == o.first && count == o.count && ntask == o.ntask &&
                grid == o.grid && fn == o.fn;
     }
 };
@@ -103,6 +105,7 @@ struct lbm_batch {
     int n = 0, device = 0, storage = 0;
     size_t argsz = 0;  // sizeof(StepArgs<R>)
     int vec[NCLASS] = {};
+    int dyn[NCLASS] = {};  // task order per size class (0 static, 1 dynamic)
     int sms = 1;
     cudaStream_t st = nullptr;
     std::vector<cudaStream_t> side;  // one per group beyond the first
@@ -115,6 +118,7 @@ struct lbm_batch {
     int *d_k = nullptr;
     double *d_tab = nullptr; // [TIME_CHUNK][4n]
     int *d_stat = nullptr;   // [n]
+    unsigned *d_ctr = nullptr; // [MAX_GROUPS][2] task counters of dynamic groups
     // pinned host staging
     char *h_args = nullptr;
     double *h_tab = nullptr;
@@ -164,8 +168,9 @@ bool any_timed(const lbm_batch *b)
     return false;
 }
 
-// Groups of (law, tile) in a fixed order; grid = enough 4-warp blocks for
-// every task, at most the resident blocks of the whole GPU (persistent).
+// Groups of (law, tile, task order) in a fixed order; grid = enough 4-warp
+// blocks for every task, at most the resident blocks of the whole GPU
+// (persistent).
 lbm_status make_plan(lbm_batch *b, Plan &p)
 {
     p = Plan();
@@ -173,19 +178,24 @@ lbm_status make_plan(lbm_batch *b, Plan &p)
     std::vector<std::pair<long long, int>> key(b->n);
     for (int i = 0; i < b->n; ++i) {
         const lbm_ctx *c = b->m[i];
-        const int v = b->vec[size_class(c->L.nx)];
-        key[i] = {(long long)c->m.law * 16 + v, i};
+        const int k = size_class(c->L.nx);
+        key[i] = {(long long)c->m.law * 32 + b->vec[k] * 2 + b->dyn[k], i};
     }
     std::stable_sort(key.begin(), key.end(),
                      [](const std::pair<long long, int> &x, const std::pair<long long, int> &y) { return x.first < y.first; });
     for (int i = 0; i < b->n; ++i) {
         const int mi = key[i].second;
         const lbm_ctx *c = b->m[mi];
-        const int law = c->m.law, v = b->vec[size_class(c->L.nx)];
-        if (p.groups.empty() || p.groups.back().law != law || p.groups.back().vec != v) {
+        const int k = size_class(c->L.nx);
+        const int law = c->m.law, v = b->vec[k];
+        const bool dyn = b->dyn[k] != 0;
+        if (p.groups.empty() || p.groups.back().law != law || p.groups.back().vec != v ||
+            p.groups.back().dyn != dyn) {
+            if ((int)p.groups.size() == MAX_GROUPS) return bfail(b, LBM_ERR_ARG, "too many groups");
             Group g;
             g.law = law;
             g.vec = v;
+            g.dyn = dyn;
             g.first = i;
             g.fn = kernel_for(b->storage, law, v);
             if (!g.fn) return bfail(b, LBM_ERR_UNSUPPORTED, "no batched kernel for this closure and tile");
@@ -260,6 +270,7 @@ lbm_status launch_group(lbm_batch *b, const Plan &p, int gi, int parity, cudaStr
     BatchList bl;
     bl.args = b->d_args + ((size_t)parity * b->n + g.first) * b->argsz;
     bl.off = b->d_off + g.first + gi;
+    bl.ctr = g.dyn ? b->d_ctr + 2 * gi : nullptr;
     bl.n = g.count;
     void *params[] = {&bl};
     BK(b, cudaLaunchKernel(g.fn, dim3(g.grid), dim3(128), params, (g.count + 1) * sizeof(int), s));
@@ -441,12 +452,14 @@ lbm_status alloc_batch(lbm_batch *b)
     BK(b, cudaMalloc((void **)&b->d_k, sizeof(int)));
     BK(b, cudaMalloc((void **)&b->d_tab, (size_t)TIME_CHUNK * 4 * n * sizeof(double)));
     BK(b, cudaMalloc((void **)&b->d_stat, n * sizeof(int)));
+    BK(b, cudaMalloc((void **)&b->d_ctr, 2 * MAX_GROUPS * sizeof(unsigned)));
     BK(b, cudaMallocHost((void **)&b->h_args, 2 * n * b->argsz));
     BK(b, cudaMallocHost((void **)&b->h_tab, (size_t)TIME_CHUNK * 4 * n * sizeof(double)));
     BK(b, cudaMallocHost((void **)&b->h_stat, n * sizeof(int)));
     BK(b, cudaMallocHost((void **)&b->h_off, (2 * n + 1) * sizeof(int)));
     BK(b, cudaMemsetAsync(b->d_g, 0, 4 * n * sizeof(double), b->st));
     BK(b, cudaMemsetAsync(b->d_k, 0, sizeof(int), b->st));
+    BK(b, cudaMemsetAsync(b->d_ctr, 0, 2 * MAX_GROUPS * sizeof(unsigned), b->st));
     BK(b, cudaStreamSynchronize(b->st));
     return LBM_OK;
 }
@@ -537,6 +550,7 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaFree(b->d_k);
     cudaFree(b->d_tab);
     cudaFree(b->d_stat);
+    cudaFree(b->d_ctr);
     cudaFreeHost(b->h_args);
     cudaFreeHost(b->h_tab);
     cudaFreeHost(b->h_stat);
@@ -567,6 +581,23 @@ lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t size_class, int32_t vec)
     return LBM_OK;
 }
 
+lbm_status lbm_batch_get_task_orders(const lbm_batch *b, int32_t *dynamic)
+{
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "null batch");
+    if (!dynamic) return bfail(const_cast<lbm_batch *>(b), LBM_ERR_ARG, "dynamic is NULL");
+    for (int k = 0; k < NCLASS; ++k) dynamic[k] = b->dyn[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_task_order(lbm_batch *b, int32_t size_class, int32_t dynamic)
+{
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "null batch");
+    if (size_class < 0 || size_class >= NCLASS) return bfail(b, LBM_ERR_ARG, "size class out of range");
+    if (dynamic != 0 && dynamic != 1) return bfail(b, LBM_ERR_ARG, "dynamic must be 0 or 1");
+    b->dyn[size_class] = dynamic;
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
 {
     Range range_("lbm_batch_tune");
@@ -589,8 +620,11 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    int chosen[NCLASS];
-    for (int k = 0; k < NCLASS; ++k) chosen[k] = b->vec[k];
+    int chosen[NCLASS], chosen_dyn[NCLASS];
+    for (int k = 0; k < NCLASS; ++k) {
+        chosen[k] = b->vec[k];
+        chosen_dyn[k] = b->dyn[k];
+    }
     const std::vector<lbm_ctx *> all = b->m;
     const int n_all = b->n;
     for (int cls = 0; cls < NCLASS && s == LBM_OK; ++cls) {
@@ -599,40 +633,44 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
         for (lbm_ctx *c : all)
             if (size_class(c->L.nx) == cls) mine.push_back(c);
         if (mine.empty()) continue;
-        const int keep = b->vec[cls];
+        const int keep = b->vec[cls], keep_dyn = b->dyn[cls];
         double best = 1e300;
-        for (size_t ti = 0; ti < tiles.size() && s == LBM_OK; ++ti) {
-            b->m = mine;
-            b->n = (int)mine.size();
-            b->vec[cls] = tiles[ti];
-            Plan p;
-            s = make_plan(b, p);
-            p.timed = false;  // trials take the time factors of the current step from the host
-            if (s == LBM_OK) s = upload_plan(b, p, u_scratch, stat_scratch);
-            if (s == LBM_OK) s = ensure_side_streams(b, (int)p.groups.size());
-            float ms = 0.f;
-            if (s == LBM_OK) {
-                for (int r = 0; r < 2 && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);  // warm-up
-                if (s == LBM_OK) cudaEventRecord(t0, b->st);
-                for (int r = 0; r < reps && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);
+        for (size_t ti = 0; ti < tiles.size() && s == LBM_OK; ++ti)
+            for (int order = 0; order < 2 && s == LBM_OK; ++order) {
+                b->m = mine;
+                b->n = (int)mine.size();
+                b->vec[cls] = tiles[ti];
+                b->dyn[cls] = order;
+                Plan p;
+                s = make_plan(b, p);
+                p.timed = false;  // trials take the time factors of the current step from the host
+                if (s == LBM_OK) s = upload_plan(b, p, u_scratch, stat_scratch);
+                if (s == LBM_OK) s = ensure_side_streams(b, (int)p.groups.size());
+                float ms = 0.f;
                 if (s == LBM_OK) {
-                    cudaEventRecord(t1, b->st);
-                    cudaError_t e = cudaEventSynchronize(t1);
-                    if (e != cudaSuccess) s = bcuda(b, e, "cudaEventSynchronize");
+                    for (int r = 0; r < 2 && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);  // warm-up
+                    if (s == LBM_OK) cudaEventRecord(t0, b->st);
+                    for (int r = 0; r < reps && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);
+                    if (s == LBM_OK) {
+                        cudaEventRecord(t1, b->st);
+                        cudaError_t e = cudaEventSynchronize(t1);
+                        if (e != cudaSuccess) s = bcuda(b, e, "cudaEventSynchronize");
+                    }
+                    if (s == LBM_OK) cudaEventElapsedTime(&ms, t0, t1);
                 }
-                if (s == LBM_OK) cudaEventElapsedTime(&ms, t0, t1);
+                b->m = all;
+                b->n = n_all;
+                b->vec[cls] = keep;
+                b->dyn[cls] = keep_dyn;
+                if (s != LBM_OK) break;
+                const double t_us = 1000.0 * ms / reps;
+                if (us && (order == 0 || t_us < us[cls * 3 + ti])) us[cls * 3 + ti] = t_us;
+                if (t_us < best) {
+                    best = t_us;
+                    chosen[cls] = tiles[ti];
+                    chosen_dyn[cls] = order;
+                }
             }
-            b->m = all;
-            b->n = n_all;
-            b->vec[cls] = keep;
-            if (s != LBM_OK) break;
-            const double t_us = 1000.0 * ms / reps;
-            if (us) us[cls * 3 + ti] = t_us;
-            if (t_us < best) {
-                best = t_us;
-                chosen[cls] = tiles[ti];
-            }
-        }
     }
     b->m = all;
     b->n = n_all;
@@ -641,7 +679,10 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (s != LBM_OK) return s;
-    for (int k = 0; k < NCLASS; ++k) b->vec[k] = chosen[k];
+    for (int k = 0; k < NCLASS; ++k) {
+        b->vec[k] = chosen[k];
+        b->dyn[k] = chosen_dyn[k];
+    }
     b->have_plan = false;  // the device arrays hold trial arguments now
     drop_graph(b);
     BK(b, cudaEventRecord(b->ev_out, b->st));

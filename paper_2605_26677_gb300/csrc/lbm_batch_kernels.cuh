@@ -4,7 +4,8 @@
 //
 // The tasks of all members of a launch form one index space: member m owns
 // global tasks [off[m], off[m+1]), off being the prefix sum of the members'
-// (row, segment) task counts. A warp takes global task t (grid-stride), finds
+// (row, segment) task counts. A warp takes global task t (grid-stride, or
+// claimed from a counter when the group runs in dynamic order), finds
 // its member by binary search in off (copied to shared memory) and runs that
 // member's task with that member's StepArgs, exactly the per-task code of the
 // single-lattice kernel, so every member's populations evolve bit for bit as
@@ -25,12 +26,11 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
     __syncthreads();
     const StepArgs<T> *args = static_cast<const StepArgs<T> *>(b.args);
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = off[b.n];
     int m = 0;
-    for (int task = gw; task < ntask; task += nw) {
-        // a warp's tasks only grow, so its member index only moves forward
+    // a warp's tasks only grow (in either order), so its member index only
+    // moves forward
+    auto run = [&](int task) {
         int lo = m, hi = b.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -48,6 +48,32 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
             step_task<S, LAW, V, true>(a, task - off[m], lane, flags);
         flags = __reduce_or_sync(FULL_MASK, flags);
         if (flags && lane == 0) atomicOr(a.status, (int)flags);
+    };
+    if (b.ctr) {
+        // dynamic: claim the next task from the group's counter, one claim
+        // ahead; the last block to finish zeroes the counters for the next
+        // launch (every claim of the launch has returned by then)
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(b.ctr, 1u);
+        t = __shfl_sync(FULL_MASK, t, 0);
+        while (t < (unsigned)ntask) {
+            unsigned nt = 0;
+            if (lane == 0) nt = atomicAdd(b.ctr, 1u);
+            run((int)t);
+            t = __shfl_sync(FULL_MASK, nt, 0);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(b.ctr + 1, 1u) == gridDim.x - 1) {
+                b.ctr[0] = 0u;
+                b.ctr[1] = 0u;
+            }
+        }
+    } else {
+        const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const int nw = gridDim.x * (blockDim.x >> 5);
+        for (int task = gw; task < ntask; task += nw) run(task);
     }
 }
 

@@ -179,6 +179,13 @@ struct StepArgs {
     const double *profile[4];
     int k16;                     // 16-bit storage: step kernel chosen for the context (0 register,
                                  // 1 staged); read by the host launcher only
+    // dynamic task claims (uniform material, register kernels): ctr2 the
+    // context's pair of device counters or nullptr, ctr_par the host-side
+    // index of the one the next dynamic launch takes (read by the launcher);
+    // ctr / ctr_next that launch's counter and the one it zeroes
+    unsigned *ctr2;
+    int *ctr_par;
+    unsigned *ctr, *ctr_next;
 };
 
 // A batch of lattices for one persistent launch
@@ -186,6 +193,8 @@ constexpr int BATCH_MAX_MEMBERS = 4096;
 struct BatchList {
     const void *args;  // StepArgs<R>[n]
     const int *off;    // n + 1 prefix sums of the members' task counts
+    unsigned *ctr;     // dynamic task order: {claims, finished blocks}, both
+                       // zero when the launch begins; nullptr: static order
     int n;
 };
 

@@ -16,6 +16,17 @@ namespace tlv {
 // 16-bit step kernel forced by the environment: LBM_STEP16=regs (register
 // kernel, 0) or LBM_STEP16=staged (shared-memory staged kernel, 1); -1 when
 // unset, and each context then uses the one lbm_init timed faster.
+// Task order forced by the environment: LBM_DYN=0 (static grid-stride, 0)
+// or LBM_DYN=1 (dynamic claims, 1); -1 when unset, and the first lbm_step
+// of each context then times both.
+inline int dyn_env_choice()
+{
+    const char *v = std::getenv("LBM_DYN");
+    if (v && !std::strcmp(v, "0")) return 0;
+    if (v && !std::strcmp(v, "1")) return 1;
+    return -1;
+}
+
 inline int step16_env_choice()
 {
     static const int k = [] {
@@ -38,6 +49,9 @@ struct lbm_ctx {
     double *ustar = nullptr;
     int *d_status = nullptr;
     double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
+    unsigned *d_ctr = nullptr; // pair of task counters of the dynamic step kernels
+    int ctr_par = 0;           // which of the pair the next dynamic launch takes
+    bool dyn = false;          // dynamic task claims (chosen by the first lbm_step, or LBM_DYN)
     double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
     int cur = 0;
     long long step = 0;
@@ -57,7 +71,7 @@ struct lbm_ctx {
     double *d_mufield = nullptr;  // per-node mu, compact FP64 (N), or nullptr
     void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
     int k16 = 0;                  // 16-bit storage: step kernel (0 register, 1 staged)
-    bool k16_pending = false;     // the next lbm_step times both 16-bit kernels first
+    bool tune_pending = true;     // the first lbm_step times the step-launch variants (tune_step)
 };
 
 

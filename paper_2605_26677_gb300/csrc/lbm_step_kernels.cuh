@@ -9,7 +9,30 @@
 #include "lbm_launch.cuh"
 
 namespace tlv {
-template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false>
+// Task order of the persistent step kernels. Static: warp w takes tasks w,
+// w + W, w + 2W, ... Dynamic (DYN): warps claim the next task from a counter
+// in device memory (one claim ahead, so that the atomic's latency overlaps
+// the current task), so a warp that runs slower takes fewer tasks and the
+// launch ends more evenly. Each launch uses one of a pair of counters and
+// zeroes the other, which the next launch in the stream uses; a launch
+// starts only after the previous one has completed (griddepcontrol.wait),
+// so every counter is zero when its launch begins.
+template <typename Fn>
+__device__ __forceinline__ void dyn_tasks(unsigned *ctr, unsigned *ctr_next, int ntask, int lane, Fn &&run)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ctr_next = 0u;
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1u);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    while (t < (unsigned)ntask) {
+        unsigned nt = 0;
+        if (lane == 0) nt = atomicAdd(ctr, 1u);
+        run((int)t);
+        t = __shfl_sync(FULL_MASK, nt, 0);
+    }
+}
+
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false, bool DYN = false>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R> a)
 {
     pdl_enter();
@@ -18,12 +41,16 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
     unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags);
+    if constexpr (DYN)
+        dyn_tasks(a.ctr, a.ctr_next, ntask, lane,
+                  [&](int task) { step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags); });
+    else
+        for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
 
-template <typename S, int LAW, int V, bool FUSE, bool MATF = false>
+template <typename S, int LAW, int V, bool FUSE, bool MATF = false, bool DYN = false>
 __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
 {
     pdl_enter();
@@ -32,7 +59,11 @@ __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * V - 1) / (32 * V));
     unsigned flags = 0;
-    for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags);
+    if constexpr (DYN)
+        dyn_tasks(a.ctr, a.ctr_next, ntask, lane,
+                  [&](int task) { step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags); });
+    else
+        for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
@@ -114,12 +145,27 @@ static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fu
     if constexpr (sizeof(S) == 2) {
         cudaError_t e;
         if (launch_step16_staged<S, LAW>(a, fuse, grid, st, e)) return e;
+    }
+    if (a.ctr2) {
+        // dynamic task claims: this launch takes the counter the previous
+        // dynamic launch zeroed (only dynamic launches touch the pair)
+        StepArgs<typename Prec<S>::R> d = a;
+        d.ctr = a.ctr2 + *a.ctr_par;
+        d.ctr_next = a.ctr2 + (*a.ctr_par ^ 1);
+        *a.ctr_par ^= 1;
+        if constexpr (sizeof(S) == 2)
+            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, true>, grid, 128, 0, st, d)
+                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, true>, grid, 128, 0, st, d);
+        else
+            return fuse ? launch_pdl(k_step<S, LAW, VEC, true, false, false, true>, grid, 128, 0, st, d)
+                        : launch_pdl(k_step<S, LAW, VEC, false, false, false, true>, grid, 128, 0, st, d);
+    }
+    if constexpr (sizeof(S) == 2)
         return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true>, grid, 128, 0, st, a)
                     : launch_pdl(k_step16<S, LAW, STEP16_V, false>, grid, 128, 0, st, a);
-    } else {
+    else
         return fuse ? launch_pdl(k_step<S, LAW, VEC, true>, grid, 128, 0, st, a)
                     : launch_pdl(k_step<S, LAW, VEC, false>, grid, 128, 0, st, a);
-    }
 }
 
 template <typename S>

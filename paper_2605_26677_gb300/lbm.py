@@ -29,12 +29,13 @@ LBM_FB_NODE, LBM_FB_EXTRAP2 = range(2)
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_material", "lbm_set_material_field",
            "lbm_set_material_field_device",
            "lbm_set_body_force",
-           "lbm_set_boundary", "lbm_set_boundary_table", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_sync",
+           "lbm_set_boundary", "lbm_set_boundary_table", "lbm_init", "lbm_init_device", "lbm_step", "lbm_step_async", "lbm_step_variant", "lbm_sync",
            "lbm_read_state", "lbm_read_state_device", "lbm_read_displacement", "lbm_read_displacement_device",
            "lbm_read_cauchy", "lbm_diagnostics", "lbm_save", "lbm_load", "lbm_info", "lbm_profile",
            "lbm_profile_read", "lbm_bytes_per_node_update", "lbm_diagnostics_state_noalloc",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_size_class",
-           "lbm_batch_get_tiles", "lbm_batch_set_tile", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_info",
+           "lbm_batch_get_tiles", "lbm_batch_set_tile", "lbm_batch_get_task_orders",
+           "lbm_batch_set_task_order", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_info",
            "lbm_adjoint_create", "lbm_adjoint_destroy", "lbm_adjoint_last_error", "lbm_adjoint_set_loss",
            "lbm_adjoint_forward", "lbm_adjoint_backward", "lbm_adjoint_info"]
 LBM_BATCH_MAX_MEMBERS = 4096
@@ -85,6 +86,7 @@ _lib.lbm_init.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 _lib.lbm_init_device.argtypes = [_ctx, C.c_void_p, C.c_void_p, C.c_int32]
 _lib.lbm_step.argtypes = [_ctx, C.c_int64]
 _lib.lbm_step_async.argtypes = [_ctx, C.c_int64]
+_lib.lbm_step_variant.argtypes = [_ctx, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 _lib.lbm_sync.argtypes = [_ctx]
 _lib.lbm_read_state.argtypes = [_ctx, C.c_void_p, C.c_void_p, _dp]
 _lib.lbm_read_state_device.argtypes = [_ctx, C.c_void_p, C.c_void_p]
@@ -113,6 +115,8 @@ _lib.lbm_batch_size_class.argtypes = [C.c_int32]
 _lib.lbm_batch_size_class.restype = C.c_int32
 _lib.lbm_batch_get_tiles.argtypes = [C.c_void_p, _ip]
 _lib.lbm_batch_set_tile.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+_lib.lbm_batch_get_task_orders.argtypes = [C.c_void_p, _ip]
+_lib.lbm_batch_set_task_order.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
 _lib.lbm_batch_tune.argtypes = [C.c_void_p, C.c_int32, _dp]
 _lib.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _ip]
 _lib.lbm_batch_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _ip, _ip]
@@ -267,6 +271,13 @@ def lbm_step_async(ctx, nsteps):
     _check(ctx, _lib.lbm_step_async(ctx, int(nsteps)))
 
 
+def lbm_step_variant(ctx):
+    """{"staged": 0/1, "dynamic": 0/1}: the step-launch variant the context runs now."""
+    st, dy = C.c_int32(), C.c_int32()
+    _check(ctx, _lib.lbm_step_variant(ctx, C.byref(st), C.byref(dy)))
+    return {"staged": st.value, "dynamic": dy.value}
+
+
 def lbm_sync(ctx):
     _check(ctx, _lib.lbm_sync(ctx))
 
@@ -413,6 +424,16 @@ def lbm_batch_get_tiles(b):
 
 def lbm_batch_set_tile(b, size_class, vec):
     _bcheck(b, _lib.lbm_batch_set_tile(b, int(size_class), int(vec)))
+
+
+def lbm_batch_get_task_orders(b):
+    v = (C.c_int32 * LBM_BATCH_CLASSES)()
+    _bcheck(b, _lib.lbm_batch_get_task_orders(b, v))
+    return list(v)
+
+
+def lbm_batch_set_task_order(b, size_class, dynamic):
+    _bcheck(b, _lib.lbm_batch_set_task_order(b, int(size_class), int(dynamic)))
 
 
 def lbm_batch_tune(b, reps=20):

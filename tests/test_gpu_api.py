@@ -271,3 +271,32 @@ def test_page_locked_host_arrays_give_the_same_results(lbm, storage):
     for x, y in zip(*res):
         assert np.all(np.isfinite(x))
         assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_dynamic_and_static_task_order_give_the_same_bits(lbm, storage, monkeypatch):
+    """The step kernels take their tasks in static grid-stride order or
+    claim them dynamically from a device counter (LBM_DYN=0 / 1 force one;
+    otherwise the first lbm_step times both); a node's update does not
+    depend on which warp runs it, so both orders give the same bits, over
+    several steps (each dynamic launch uses the counter the previous one
+    zeroed) and with the variant choice's trial launches in between."""
+    nx, ny = 300, 41
+    U0 = smooth_field(nx, ny, seed=12, amp=0.04, periodic=False)
+    res = []
+    for dyn in ("1", "0"):
+        monkeypatch.setenv("LBM_DYN", dyn)
+        L = make(lbm, nx, ny, storage=storage, omega=1.9)
+        lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+        lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.01))
+        lbm.lbm_init(L.ctx, U0)
+        for n in (1, 2, 7):
+            lbm.lbm_step(L.ctx, n)
+        v = lbm.lbm_step_variant(L.ctx)
+        assert v["dynamic"] == int(dyn)
+        assert v["staged"] in ((0, 1) if dyn == "0" and storage >= 2 else (0,))
+        U, P, _ = lbm.lbm_read_state(L.ctx)
+        res.append((U, P, lbm.lbm_read_displacement(L.ctx)))
+        L.close()
+    for x, y in zip(*res):
+        assert np.array_equal(x.view(np.uint64), y.view(np.uint64))

@@ -86,13 +86,17 @@ def individual(lbm, cases, storage, steps):
     return s
 
 
-def batched(lbm, cases, storage, steps, graph_steps=0, tile=None, calls=1):
+def batched(lbm, cases, storage, steps, graph_steps=0, tile=None, calls=1, dynamic=None):
     Ls = [make_ctx(lbm, c, storage) for c in cases]
     b = lbm.lbm_batch_create([L.ctx for L in Ls])
     try:
         if tile is not None:
             for k in range(lbm.LBM_BATCH_CLASSES):
                 lbm.lbm_batch_set_tile(b, k, tile)
+        if dynamic is not None:
+            for k in range(lbm.LBM_BATCH_CLASSES):
+                lbm.lbm_batch_set_task_order(b, k, dynamic)
+            assert lbm.lbm_batch_get_task_orders(b) == [dynamic] * lbm.LBM_BATCH_CLASSES
         for i in range(calls):
             st = lbm.lbm_batch_step(b, steps, graph_steps)
             assert all(s == 0 for s in st)
@@ -122,6 +126,22 @@ def test_every_tile_equals_individual(lbm, storage):
     for tile in TILES[storage]:
         got, _ = batched(lbm, cases, storage, 37, tile=tile)
         same(got, ref)
+
+
+@pytest.mark.parametrize("storage", [F64, F32, BF16, F16])
+def test_dynamic_task_order_equals_individual(lbm, storage):
+    """Tasks claimed from the group counters: every member bit for bit as in
+    its own runs, for every tile, with direct launches and graph replays and
+    over calls of an odd number of steps (the counters are reset by each
+    launch's last block, whatever the step parity)."""
+    cases = mixed_members()
+    ref = individual(lbm, cases, storage, 74)
+    for tile in TILES[storage]:
+        got, _ = batched(lbm, cases, storage, 37, tile=tile, calls=2, dynamic=1)
+        same(got, ref)
+    got, info = batched(lbm, cases, storage, 37, graph_steps=8, calls=2, dynamic=1)
+    same(got, ref)
+    assert info["graphs"] == 1
 
 
 @pytest.mark.parametrize("storage", [F64, F32])
@@ -168,6 +188,7 @@ def test_tuning_keeps_states(lbm):
         tiles, us = lbm.lbm_batch_tune(b, reps=5)
         for k, v in enumerate(tiles):
             assert v in TILES[F32]
+        assert set(lbm.lbm_batch_get_task_orders(b)) <= {0, 1}
         present = {lbm.lbm_batch_size_class(c.nx) for c in cases}
         for k in range(lbm.LBM_BATCH_CLASSES):
             assert (us[k] > 0).all() == (k in present)
@@ -228,6 +249,11 @@ def test_batch_argument_errors(lbm):
             lbm.lbm_batch_set_tile(b, 0, 3)
         with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
             lbm.lbm_batch_set_tile(b, 5, 1)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_set_task_order(b, 5, 0)
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.lbm_batch_set_task_order(b, 0, 2)
+        assert lbm.lbm_batch_get_task_orders(b) == [0] * lbm.LBM_BATCH_CLASSES
         lbm.lbm_batch_destroy(b)
     finally:
         for L in (a, b64, ex, fresh):
