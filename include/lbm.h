@@ -198,8 +198,8 @@ lbm_status lbm_init_device(lbm_ctx *ctx, const double *U0_dev, const double *u0_
  * latched device status. With uniform material and the node form of F^b,
  * the context's first call with nsteps > 0 (after its first lbm_init or
  * lbm_init_device) first times the step-launch variants, which give
- * identical results: the task order (static, or claimed dynamically from a
- * device counter) and, with BF16 or FP16 storage, the register or the
+ * identical results: the task order (static, or claimed dynamically from
+ * device counters) and, with BF16 or FP16 storage, the register or the
  * shared-memory staged kernel; a few trial steps leave the state untouched,
  * and the fastest is kept for the context's life (the trials take a
  * u*-sized scratch allocation while they run). Until then, and for
@@ -212,8 +212,9 @@ lbm_status lbm_step_async(lbm_ctx *ctx, int64_t nsteps);
 
 /* The step-launch variant the context runs now (host outputs, either may be
  * NULL): *staged = 1 for the shared-memory staged 16-bit kernel, 0 for the
- * register kernel; *dynamic = 1 for dynamic task order, 0 for static. No
- * device work. */
+ * register kernel; *dynamic = 0 for static task order, else the number of
+ * device counters the dynamic claims are spread over (1 or 4; 1 only for the
+ * 16-bit register kernel). No device work. */
 lbm_status lbm_step_variant(const lbm_ctx *ctx, int32_t *staged, int32_t *dynamic);
 
 /* Wait for the context's stream and return the latched device status. */

@@ -560,6 +560,8 @@ lbm_status backward_body(lbm_adjoint *a, double *g_mu_dev, double *g_v0_dev)
     ai.ia.order = a->order;
     ai.ia.xper = c->edge[LBM_EDGE_LEFT].kind == LBM_BC_PERIODIC;
     ai.ia.yper = c->edge[LBM_EDGE_BOTTOM].kind == LBM_BC_PERIODIC;
+    ai.ia.y0 = 0;
+    ai.ia.y1 = c->L.ny;
     ai.a0 = a->A[cur];
     ai.ubar = a->ubar;
     ai.gmu = a->gmu;

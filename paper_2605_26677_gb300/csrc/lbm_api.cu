@@ -123,8 +123,8 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.L = c->L;
     const double w = c->cfg.omega;
     relax_pair<T>(w, a.omega, a.one_m_omega);
-    a.inv2c = (T)(0.5 / c->cfg.c);
-    a.quarter = (T)0.25;
+    a.wq = a.omega * T(0.25);  // exact: a power-of-two scaling of the rounded omega
+    a.wc = (T)(w * 0.5 / c->cfg.c);
     a.hdtb1 = (T)(0.5 * c->dt * c->b[0]);
     a.hdtb2 = (T)(0.5 * c->dt * c->b[1]);
     a.src1 = (T)(c->dt * (2.0 - w) * 0.125 * c->b[0]);
@@ -147,6 +147,7 @@ StepArgs<T> step_args(const lbm_ctx *c, int cur)
     a.gdev = nullptr;
     a.k16 = c->k16;
     a.ctr2 = c->dyn ? c->d_ctr : nullptr;
+    a.dyn_ns = c->dyn ? c->dyn : DYN_STRIPES;
     a.ctr_par = const_cast<int *>(&c->ctr_par);  // advanced by the launcher of each dynamic launch
     a.ctr = nullptr;
     a.ctr_next = nullptr;
@@ -504,9 +505,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out)
     CKC(cudaMalloc((void **)&c->ustar, ubytes));
     CKC(cudaMalloc((void **)&c->d_status, sizeof(int)));
     CKC(cudaMalloc((void **)&c->d_diag, (size_t)(diag_blocks(c->L) * 10 + 10) * sizeof(double)));
-    CKC(cudaMalloc((void **)&c->d_ctr, 2 * sizeof(unsigned)));
-    CKC(cudaMemset(c->d_ctr, 0, 2 * sizeof(unsigned)));
-    c->dyn = tlv::dyn_env_choice() == 1;  // until the first lbm_step chooses
+    CKC(cudaMalloc((void **)&c->d_ctr, 2 * DYN_SET_WORDS * sizeof(unsigned)));
+    CKC(cudaMemset(c->d_ctr, 0, 2 * DYN_SET_WORDS * sizeof(unsigned)));
+    c->dyn = tlv::dyn_env_choice() == 1 ? DYN_STRIPES : 0;  // until the first lbm_step chooses
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->st));
     CKC(cudaMemsetAsync(c->ustar, 0, ubytes, c->st));
@@ -535,6 +536,11 @@ void lbm_destroy(lbm_ctx *c)
     for (int e = 0; e < 4; ++e) cudaFree(c->d_profile[e]);
     cudaFree(c->d_mufield);
     cudaFree(c->d_muplane);
+    if (c->st_copy) {
+        cudaStreamSynchronize(c->st_copy);
+        cudaStreamDestroy(c->st_copy);
+    }
+    for (cudaEvent_t e : c->ev_band) cudaEventDestroy(e);
     delete c;
 }
 
@@ -697,7 +703,7 @@ lbm_status lbm_set_boundary_table(lbm_ctx *c, int32_t edge, int32_t n, const dou
     return LBM_OK;
 }
 
-static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
+static InitArgs init_args(const lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
 {
     InitArgs a;
     a.U0 = U0_dev;
@@ -716,22 +722,94 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
     a.order = order;
     a.xper = xper(c);
     a.yper = yper(c);
-    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
-    CK(c, launch_init(c->cfg.storage, a, c->st));
+    a.y0 = 0;
+    a.y1 = c->L.ny;
+    return a;
+}
+
+static void init_done(lbm_ctx *c)
+{
     c->cur = 0;
     c->step = 0;
     c->initialized = true;
     c->ghosts_dirty = true;
+}
+
+static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0_dev, int32_t order)
+{
+    const InitArgs a = init_args(c, U0_dev, u0_dev, order);
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    CK(c, launch_init(c->cfg.storage, a, c->st));
+    init_done(c);
+    return LBM_OK;
+}
+
+// lbm_init from host arrays: the copy of U0 (and u0) in row bands on the
+// context's copy stream, overlapped with the initialization of the bands
+// already copied on the context's stream. Band b's stencils read up to two
+// rows past it (one-sided at a non-periodic edge, one row when periodic), so
+// it starts once band b + 1 has arrived; with periodic rows band 0 also needs
+// the last row and goes last. Bands hold at least INIT_BAND_MIN_ROWS rows, so
+// the rows a band's stencils reach lie in the next band.
+constexpr int INIT_BANDS = 8;
+constexpr int INIT_BAND_MIN_ROWS = 4;
+constexpr size_t INIT_PIPELINE_MIN_BYTES = size_t(64) << 20;
+
+static lbm_status init_from_host(lbm_ctx *c, const double *U0, const double *u0, int32_t order, double *dU,
+                                 double *du)
+{
+    const int nx = c->L.nx, ny = c->L.ny;
+    const size_t N = (size_t)nx * ny;
+    int K = INIT_BANDS;
+    if (6 * N * sizeof(double) < INIT_PIPELINE_MIN_BYTES) K = 1;
+    if (ny / INIT_BAND_MIN_ROWS < K) K = ny / INIT_BAND_MIN_ROWS;
+    if (K <= 1) {
+        CK(c, cudaMemcpyAsync(dU, U0, 6 * N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        if (u0) CK(c, cudaMemcpyAsync(du, u0, 2 * N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        return init_common(c, dU, du, order);
+    }
+    if (!c->st_copy) CK(c, cudaStreamCreateWithFlags(&c->st_copy, cudaStreamNonBlocking));
+    while ((int)c->ev_band.size() < K + 1) {
+        cudaEvent_t e;
+        CK(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->ev_band.push_back(e);
+    }
+    // the copies follow the allocations (and earlier work) of the context's stream
+    CK(c, cudaEventRecord(c->ev_band[K], c->st));
+    CK(c, cudaStreamWaitEvent(c->st_copy, c->ev_band[K], 0));
+    std::vector<int> y(K + 1);
+    for (int b = 0; b <= K; ++b) y[b] = (int)((long long)ny * b / K);
+    for (int b = 0; b < K; ++b) {
+        const size_t off = (size_t)y[b] * nx, len = (size_t)(y[b + 1] - y[b]) * nx * sizeof(double);
+        for (int k = 0; k < 6; ++k)
+            CK(c, cudaMemcpyAsync(dU + k * N + off, U0 + k * N + off, len, cudaMemcpyHostToDevice, c->st_copy));
+        if (u0)
+            for (int k = 0; k < 2; ++k)
+                CK(c, cudaMemcpyAsync(du + k * N + off, u0 + k * N + off, len, cudaMemcpyHostToDevice, c->st_copy));
+        CK(c, cudaEventRecord(c->ev_band[b], c->st_copy));
+    }
+    InitArgs a = init_args(c, dU, du, order);
+    CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    for (int i = 0; i < K; ++i) {
+        const int b = a.yper ? (i + 1) % K : i;  // periodic rows: band 0 last
+        const int need = (a.yper && b == 0) ? K - 1 : std::min(b + 1, K - 1);
+        CK(c, cudaStreamWaitEvent(c->st, c->ev_band[need], 0));
+        a.y0 = y[b];
+        a.y1 = y[b + 1];
+        CK(c, launch_init(c->cfg.storage, a, c->st));
+    }
+    init_done(c);
     return LBM_OK;
 }
 
 // Step-launch variants: which 16-bit kernel (registers, or rows staged in
 // shared memory) and which task order (static grid-stride, or dynamic claims
-// from a device counter). All give bit-identical states, and which is
-// fastest depends on the lattice (BF16, fraction of the copy bandwidth:
-// 4096 x 2048 clamped register static 0.838, register dynamic 0.907, staged
-// 0.852; 8192^2 periodic 0.909, 0.709, 0.81; FP32 4096 x 2048 clamped static
-// 0.954, dynamic 0.934; 8192^2 periodic 0.954, 0.958). The first lbm_step of a
+// over DYN_STRIPES counters, or for the 16-bit register kernel also over one
+// counter). All give bit-identical states, and which is fastest depends on
+// the lattice (fraction of the copy bandwidth, static / one counter / striped:
+// BF16 4096 x 2048 clamped 0.909 / 0.923 / 0.856, BF16 8192^2 periodic
+// 0.918 / 0.718 / 0.924, FP32 4096 x 2048 clamped 0.955 / 0.937 / 0.979,
+// FP32 8192^2 periodic 0.960 / 0.958 / 1.009). The first lbm_step of a
 // context times the candidates on its lattice and keeps the fastest for the
 // context's life. The trials read the current buffer, whose ghost cells are
 // refreshed first exactly as the first step would, and write only the other
@@ -745,8 +823,8 @@ static lbm_status init_common(lbm_ctx *c, const double *U0_dev, const double *u0
 namespace {
 
 struct StepVariant {
-    int k16;
-    bool dyn;
+    int k16;  // 16-bit kernel: 0 register, 1 staged
+    int dyn;  // 0 static order, else the stripes of the dynamic claims
 };
 
 template <typename T>
@@ -754,11 +832,14 @@ lbm_status tune_step(lbm_ctx *c)
 {
     if (c->cfg.fb_mode != LBM_FB_NODE || c->d_muplane) return LBM_OK;
     std::vector<StepVariant> cand;
-    const int env16 = tlv::step16_env_choice(), envdyn = tlv::dyn_env_choice();
+    const int env16 = tlv::step16_env_choice(), envdyn = tlv::dyn_env_choice(), envns = tlv::stripes_env_choice();
     for (int k16 = 0; k16 < (c->eb == 2 ? 2 : 1); ++k16)
-        for (int d = 0; d < 2; ++d) {
-            if ((env16 >= 0 && k16 != env16) || (envdyn >= 0 && d != envdyn) || (k16 == 1 && d == 1)) continue;
-            cand.push_back({k16, d == 1});
+        for (int d : {0, DYN_STRIPES, 1}) {
+            if (d == 1 && (c->eb != 2 || DYN_STRIPES == 1)) continue;  // one counter: 16-bit kernels only
+            if (k16 == 1 && d != 0) continue;                         // the staged kernel keeps static order
+            if ((env16 >= 0 && k16 != env16) || (envdyn >= 0 && (d != 0) != (envdyn == 1))) continue;
+            if (envns >= 0 && d != 0 && d != envns) continue;
+            cand.push_back({k16, d});
         }
     if (cand.size() == 1) {
         c->k16 = cand[0].k16;
@@ -796,6 +877,7 @@ lbm_status tune_step(lbm_ctx *c)
     auto set = [&](const StepVariant &v) {
         a.k16 = v.k16;
         a.ctr2 = v.dyn ? c->d_ctr : nullptr;
+        a.dyn_ns = v.dyn ? v.dyn : DYN_STRIPES;
     };
     // a warm-up step of each, then three rounds of three steps of each
     // variant, interleaved so that clock changes weigh on all alike
@@ -863,15 +945,12 @@ lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t orde
     const size_t N = (size_t)c->L.nx * c->L.ny;
     double *dU = nullptr, *du = nullptr;
     CK(c, cudaMallocAsync((void **)&dU, 6 * N * sizeof(double), c->st));
-    cudaError_t e = cudaMemcpyAsync(dU, U0, 6 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    if (e == cudaSuccess && u0) {
-        e = cudaMallocAsync((void **)&du, 2 * N * sizeof(double), c->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(du, u0, 2 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    }
-    if (e == cudaSuccess) s = init_common(c, dU, du, order);
+    cudaError_t e = u0 ? cudaMallocAsync((void **)&du, 2 * N * sizeof(double), c->st) : cudaSuccess;
+    if (e == cudaSuccess) s = init_from_host(c, U0, u0, order, dU, du);
+    if (s != LBM_OK) cudaStreamSynchronize(c->st_copy ? c->st_copy : c->st);  // copies still in flight
     cudaFreeAsync(dU, c->st);
     if (du) cudaFreeAsync(du, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copying the initial state");
+    if (e != cudaSuccess) return cuda_fail(c, e, "allocating the initial state");
     if (s != LBM_OK) return s;
     return sync_status(c);
 }
@@ -915,7 +994,7 @@ lbm_status lbm_step_variant(const lbm_ctx *c, int32_t *staged, int32_t *dynamic)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (staged) *staged = c->k16;
-    if (dynamic) *dynamic = c->dyn ? 1 : 0;
+    if (dynamic) *dynamic = c->dyn;
     return LBM_OK;
 }
 

@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(128) k_init(const InitArgs a)
     T *fout = static_cast<T *>(a.fout);
     const double dt = a.dt;
     const R c = (R)a.c, w = (R)a.omega;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+    const long long n1 = (long long)a.y1 * nx;
+    for (long long n = (long long)a.y0 * nx + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n1;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
         R f[4][6];  // f^0 - f_rest
@@ -249,7 +250,11 @@ static int grid_for(long long n, int threads)
 
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st)
 {
-    const int g = grid_for((long long)a.L.nx * a.L.ny, 128);
+    // the kernel writes rows [y0, y1) and reads U0 around them: a range
+    // outside the lattice is an error, an empty one a no-op
+    if (a.y0 < 0 || a.y1 > a.L.ny || a.y1 < a.y0) return cudaErrorInvalidValue;
+    if (a.y1 == a.y0) return cudaSuccess;
+    const int g = grid_for((long long)a.L.nx * (a.y1 - a.y0), 128);
     return with_storage(storage, [&](auto tag) {
         k_init<decltype(tag)><<<g, 128, 0, st>>>(a);
         return cudaGetLastError();

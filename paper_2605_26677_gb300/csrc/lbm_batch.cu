@@ -29,6 +29,8 @@ constexpr int NCLASS = LBM_BATCH_CLASSES;
 constexpr int CLASS_MAX_NX[NCLASS - 1] = {48, 96, 192, 384};
 constexpr int TIME_CHUNK = 1024;  // steps of edge time factors per upload
 constexpr int MAX_GROUPS = 64;    // (closure, tile, order) groups; 6 x 3 x 2 exist
+// per group: DYN_STRIPES claim counters and a finished-blocks counter
+constexpr int GROUP_CTR_WORDS = (DYN_STRIPES + 1) * DYN_CTR_STRIDE;
 
 int size_class(int nx)
 {
@@ -118,7 +120,7 @@ struct lbm_batch {
     int *d_k = nullptr;
     double *d_tab = nullptr; // [TIME_CHUNK][4n]
     int *d_stat = nullptr;   // [n]
-    unsigned *d_ctr = nullptr; // [MAX_GROUPS][2] task counters of dynamic groups
+    unsigned *d_ctr = nullptr; // [MAX_GROUPS][GROUP_CTR_WORDS] task counters of dynamic groups
     // pinned host staging
     char *h_args = nullptr;
     double *h_tab = nullptr;
@@ -270,7 +272,7 @@ lbm_status launch_group(lbm_batch *b, const Plan &p, int gi, int parity, cudaStr
     BatchList bl;
     bl.args = b->d_args + ((size_t)parity * b->n + g.first) * b->argsz;
     bl.off = b->d_off + g.first + gi;
-    bl.ctr = g.dyn ? b->d_ctr + 2 * gi : nullptr;
+    bl.ctr = g.dyn ? b->d_ctr + (size_t)gi * GROUP_CTR_WORDS : nullptr;
     bl.n = g.count;
     void *params[] = {&bl};
     BK(b, cudaLaunchKernel(g.fn, dim3(g.grid), dim3(128), params, (g.count + 1) * sizeof(int), s));
@@ -452,14 +454,14 @@ lbm_status alloc_batch(lbm_batch *b)
     BK(b, cudaMalloc((void **)&b->d_k, sizeof(int)));
     BK(b, cudaMalloc((void **)&b->d_tab, (size_t)TIME_CHUNK * 4 * n * sizeof(double)));
     BK(b, cudaMalloc((void **)&b->d_stat, n * sizeof(int)));
-    BK(b, cudaMalloc((void **)&b->d_ctr, 2 * MAX_GROUPS * sizeof(unsigned)));
+    BK(b, cudaMalloc((void **)&b->d_ctr, (size_t)MAX_GROUPS * GROUP_CTR_WORDS * sizeof(unsigned)));
     BK(b, cudaMallocHost((void **)&b->h_args, 2 * n * b->argsz));
     BK(b, cudaMallocHost((void **)&b->h_tab, (size_t)TIME_CHUNK * 4 * n * sizeof(double)));
     BK(b, cudaMallocHost((void **)&b->h_stat, n * sizeof(int)));
     BK(b, cudaMallocHost((void **)&b->h_off, (2 * n + 1) * sizeof(int)));
     BK(b, cudaMemsetAsync(b->d_g, 0, 4 * n * sizeof(double), b->st));
     BK(b, cudaMemsetAsync(b->d_k, 0, sizeof(int), b->st));
-    BK(b, cudaMemsetAsync(b->d_ctr, 0, 2 * MAX_GROUPS * sizeof(unsigned), b->st));
+    BK(b, cudaMemsetAsync(b->d_ctr, 0, (size_t)MAX_GROUPS * GROUP_CTR_WORDS * sizeof(unsigned), b->st));
     BK(b, cudaStreamSynchronize(b->st));
     return LBM_OK;
 }

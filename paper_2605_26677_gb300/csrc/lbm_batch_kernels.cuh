@@ -28,10 +28,11 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
     const int lane = threadIdx.x & 31;
     const int ntask = off[b.n];
     int m = 0;
-    // a warp's tasks only grow (in either order), so its member index only
-    // moves forward
     auto run = [&](int task) {
-        int lo = m, hi = b.n - 1;
+        // a warp's tasks grow except when it wraps from the last stripe to
+        // the first (dynamic order): search from its member index onwards,
+        // or from the start after a wrap
+        int lo = (task >= off[m]) ? m : 0, hi = b.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (off[mid] <= task)
@@ -49,29 +50,22 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
         flags = __reduce_or_sync(FULL_MASK, flags);
         if (flags && lane == 0) atomicOr(a.status, (int)flags);
     };
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b.ctr) {
-        // dynamic: claim the next task from the group's counter, one claim
-        // ahead; the last block to finish zeroes the counters for the next
-        // launch (every claim of the launch has returned by then)
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(b.ctr, 1u);
-        t = __shfl_sync(FULL_MASK, t, 0);
-        while (t < (unsigned)ntask) {
-            unsigned nt = 0;
-            if (lane == 0) nt = atomicAdd(b.ctr, 1u);
-            run((int)t);
-            t = __shfl_sync(FULL_MASK, nt, 0);
-        }
+        // dynamic: claim_tasks on the group's counters; the last block to
+        // finish zeroes them for the next launch (every claim of the launch
+        // has returned by then)
+        claim_tasks<DYN_STRIPES>(b.ctr, ntask, lane, run);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (atomicAdd(b.ctr + 1, 1u) == gridDim.x - 1) {
-                b.ctr[0] = 0u;
-                b.ctr[1] = 0u;
+            unsigned *done = b.ctr + DYN_STRIPES * DYN_CTR_STRIDE;
+            if (atomicAdd(done, 1u) == gridDim.x - 1) {
+                for (int j = 0; j < DYN_STRIPES; ++j) b.ctr[j * DYN_CTR_STRIDE] = 0u;
+                *done = 0u;
             }
         }
     } else {
-        const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
         const int nw = gridDim.x * (blockDim.x >> 5);
         for (int task = gw; task < ntask; task += nw) run(task);
     }

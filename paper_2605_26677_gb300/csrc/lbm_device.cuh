@@ -163,7 +163,8 @@ struct StepArgs {
                                  // material field: the adjoint's recomputed steps) skips it
     int *status;                 // latched ST_* bits
     Layout L;
-    T omega, one_m_omega, inv2c, quarter;
+    T omega, one_m_omega;        // the pair of relax_pair
+    T wq, wc;                    // omega / 4 and omega / (2c) of the collision
     T hdtb1, hdtb2;              // (dt/2) b
     T src1, src2;                // dt (2 - omega) b / 8  (Eq. 14, w = 1/8)
     T lam, mu, c;
@@ -180,21 +181,33 @@ struct StepArgs {
     int k16;                     // 16-bit storage: step kernel chosen for the context (0 register,
                                  // 1 staged); read by the host launcher only
     // dynamic task claims (uniform material, register kernels): ctr2 the
-    // context's pair of device counters or nullptr, ctr_par the host-side
-    // index of the one the next dynamic launch takes (read by the launcher);
-    // ctr / ctr_next that launch's counter and the one it zeroes
+    // context's two counter sets (2 x DYN_SET_WORDS words) or nullptr,
+    // ctr_par the host-side index of the set the next dynamic launch takes
+    // (read by the launcher); ctr / ctr_next that launch's set and the one it
+    // zeroes
     unsigned *ctr2;
     int *ctr_par;
+    int dyn_ns;                  // stripes of the claims: 1 or DYN_STRIPES (16-bit kernels;
+                                 // the others always use DYN_STRIPES)
     unsigned *ctr, *ctr_next;
 };
+
+// Dynamic task claims (see claim_tasks): the task list is split into
+// DYN_STRIPES contiguous stripes, each with its own claim counter, and the
+// counters sit DYN_CTR_STRIDE words (256 bytes) apart so that no two share a
+// cache line. One set of counters is DYN_SET_WORDS words.
+constexpr int DYN_STRIPES = 4;
+constexpr int DYN_CTR_STRIDE = 64;
+constexpr int DYN_SET_WORDS = DYN_STRIPES * DYN_CTR_STRIDE;
 
 // A batch of lattices for one persistent launch
 constexpr int BATCH_MAX_MEMBERS = 4096;
 struct BatchList {
     const void *args;  // StepArgs<R>[n]
     const int *off;    // n + 1 prefix sums of the members' task counts
-    unsigned *ctr;     // dynamic task order: {claims, finished blocks}, both
-                       // zero when the launch begins; nullptr: static order
+    unsigned *ctr;     // dynamic task order: DYN_STRIPES claim counters and a
+                       // finished-blocks counter, DYN_CTR_STRIDE words apart,
+                       // all zero when the launch begins; nullptr: static order
     int n;
 };
 
@@ -304,6 +317,11 @@ __device__ __forceinline__ void piola_inv(const V G[4], const LawP<R> &m, V P[4]
 
 // First Piola stress from G = F - I (Appendix A), written so that the rest
 // state does not cancel catastrophically: J - 1 = G11 + G22 + G11 G22 - G12 G21.
+// 1 / x rounded to nearest (the value R(1) / x has under IEEE rules) by the
+// reciprocal intrinsics, which need fewer instructions than a division
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // Returns J - 1 in dJ.
 template <int LAW, typename R>
 __device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, const LawP<R> &m, R &P11, R &P12,
@@ -336,7 +354,7 @@ __device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, const LawP
         // Eq. (A.5) / (A.6): P = mu (F - H) + a H, H = F^{-T} = cof(F) / J,
         // a = (lambda/2)(J^2 - 1) (NH) or lambda log J (log-NH)
         const R J = R(1) + dJ;
-        const R invJ = R(1) / J;
+        const R invJ = rcp_rn(J);
         R a;
         if (LAW == LAW_NH)
             a = R(0.5) * lam * dJ * (R(2) + dJ);

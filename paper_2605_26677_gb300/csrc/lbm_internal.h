@@ -15,15 +15,24 @@
 namespace tlv {
 // 16-bit step kernel forced by the environment: LBM_STEP16=regs (register
 // kernel, 0) or LBM_STEP16=staged (shared-memory staged kernel, 1); -1 when
-// unset, and each context then uses the one lbm_init timed faster.
+// unset, and each context then uses the one its first lbm_step timed faster.
 // Task order forced by the environment: LBM_DYN=0 (static grid-stride, 0)
 // or LBM_DYN=1 (dynamic claims, 1); -1 when unset, and the first lbm_step
-// of each context then times both.
+// of each context then times both. LBM_DYN_STRIPES=1 or 4 restricts the
+// dynamic claims to that many counters (returned; -1 when unset).
 inline int dyn_env_choice()
 {
     const char *v = std::getenv("LBM_DYN");
     if (v && !std::strcmp(v, "0")) return 0;
     if (v && !std::strcmp(v, "1")) return 1;
+    return -1;
+}
+
+inline int stripes_env_choice()
+{
+    const char *v = std::getenv("LBM_DYN_STRIPES");
+    if (v && !std::strcmp(v, "1")) return 1;
+    if (v && !std::strcmp(v, "4")) return 4;
     return -1;
 }
 
@@ -49,9 +58,10 @@ struct lbm_ctx {
     double *ustar = nullptr;
     int *d_status = nullptr;
     double *d_diag = nullptr; // diag_blocks * 10 partials + 10 results
-    unsigned *d_ctr = nullptr; // pair of task counters of the dynamic step kernels
+    unsigned *d_ctr = nullptr; // two counter sets of the dynamic step kernels (2 x DYN_SET_WORDS)
     int ctr_par = 0;           // which of the pair the next dynamic launch takes
-    bool dyn = false;          // dynamic task claims (chosen by the first lbm_step, or LBM_DYN)
+    int dyn = 0;               // task order: 0 static, else dynamic claims over that many
+                               // counter stripes (chosen by the first lbm_step, or LBM_DYN)
     double *d_profile[4] = {nullptr, nullptr, nullptr, nullptr};
     int cur = 0;
     long long step = 0;
@@ -72,6 +82,8 @@ struct lbm_ctx {
     void *d_muplane = nullptr;    // the same in the compute type, u* plane layout
     int k16 = 0;                  // 16-bit storage: step kernel (0 register, 1 staged)
     bool tune_pending = true;     // the first lbm_step times the step-launch variants (tune_step)
+    cudaStream_t st_copy = nullptr;     // lbm_init's banded host copies (created on first use)
+    std::vector<cudaEvent_t> ev_band;   // their per-band events (+ one for the fork)
 };
 
 
@@ -108,6 +120,8 @@ struct InitArgs {
     Material m;
     double c, dt, dx, omega, b1, b2;
     int order, xper, yper;
+    int y0, y1;         // rows [y0, y1) written by this launch (its stencils read
+                        // U0 one or two rows beyond them)
 };
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t st);
 // per-node mu (compact FP64) -> compute-type plane in the u* layout (zero padding)

@@ -10,26 +10,19 @@
 
 namespace tlv {
 // Task order of the persistent step kernels. Static: warp w takes tasks w,
-// w + W, w + 2W, ... Dynamic (DYN): warps claim the next task from a counter
-// in device memory (one claim ahead, so that the atomic's latency overlaps
-// the current task), so a warp that runs slower takes fewer tasks and the
-// launch ends more evenly. Each launch uses one of a pair of counters and
-// zeroes the other, which the next launch in the stream uses; a launch
-// starts only after the previous one has completed (griddepcontrol.wait),
-// so every counter is zero when its launch begins.
-template <typename Fn>
+// w + W, w + 2W, ... Dynamic (DYN): warps claim tasks from counters in device
+// memory (claim_tasks; the 16-bit kernels over one stripe or DYN_STRIPES, the
+// others over DYN_STRIPES). Each launch uses one of two counter sets and zeroes
+// the other, which the next launch in the stream uses; a launch starts only
+// after the previous one has completed (griddepcontrol.wait), so every
+// counter is zero when its launch begins.
+template <int NS, typename Fn>
 __device__ __forceinline__ void dyn_tasks(unsigned *ctr, unsigned *ctr_next, int ntask, int lane, Fn &&run)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ctr_next = 0u;
-    unsigned t = 0;
-    if (lane == 0) t = atomicAdd(ctr, 1u);
-    t = __shfl_sync(FULL_MASK, t, 0);
-    while (t < (unsigned)ntask) {
-        unsigned nt = 0;
-        if (lane == 0) nt = atomicAdd(ctr, 1u);
-        run((int)t);
-        t = __shfl_sync(FULL_MASK, nt, 0);
-    }
+    // all DYN_STRIPES counters of the next set, whatever NS: the launches of
+    // a context may alternate between stripe counts
+    if (blockIdx.x == 0 && threadIdx.x < DYN_STRIPES) ctr_next[threadIdx.x * DYN_CTR_STRIDE] = 0u;
+    claim_tasks<NS>(ctr, ntask, lane, run);
 }
 
 template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false, bool DYN = false>
@@ -42,15 +35,16 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Prec<S>::R
     const int ntask = a.L.ny * ((a.L.nx + 32 * VEC - 1) / (32 * VEC));  // < 2^31 (checked at creation)
     unsigned flags = 0;
     if constexpr (DYN)
-        dyn_tasks(a.ctr, a.ctr_next, ntask, lane,
-                  [&](int task) { step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags); });
+        dyn_tasks<DYN_STRIPES>(a.ctr, a.ctr_next, ntask, lane,
+                               [&](int task) { step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags); });
     else
         for (int task = gw; task < ntask; task += nw) step_task<S, LAW, VEC, FUSE, MATF, NOQ>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
     if (flags && lane == 0) atomicOr(a.status, (int)flags);
 }
 
-template <typename S, int LAW, int V, bool FUSE, bool MATF = false, bool DYN = false>
+// DYN: 0 static order, else dynamic claims over DYN stripes (1 or DYN_STRIPES)
+template <typename S, int LAW, int V, bool FUSE, bool MATF = false, int DYN = 0>
 __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
 {
     pdl_enter();
@@ -59,9 +53,9 @@ __global__ void __launch_bounds__(128, 4) k_step16(const StepArgs<float> a)
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int ntask = a.L.ny * ((a.L.nx + 32 * V - 1) / (32 * V));
     unsigned flags = 0;
-    if constexpr (DYN)
-        dyn_tasks(a.ctr, a.ctr_next, ntask, lane,
-                  [&](int task) { step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags); });
+    if constexpr (DYN > 0)
+        dyn_tasks<DYN>(a.ctr, a.ctr_next, ntask, lane,
+                       [&](int task) { step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags); });
     else
         for (int task = gw; task < ntask; task += nw) step16_task<S, LAW, V, FUSE, MATF>(a, task, lane, flags);
     flags = __reduce_or_sync(FULL_MASK, flags);
@@ -150,12 +144,16 @@ static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fu
         // dynamic task claims: this launch takes the counter the previous
         // dynamic launch zeroed (only dynamic launches touch the pair)
         StepArgs<typename Prec<S>::R> d = a;
-        d.ctr = a.ctr2 + *a.ctr_par;
-        d.ctr_next = a.ctr2 + (*a.ctr_par ^ 1);
+        d.ctr = a.ctr2 + *a.ctr_par * DYN_SET_WORDS;
+        d.ctr_next = a.ctr2 + (*a.ctr_par ^ 1) * DYN_SET_WORDS;
         *a.ctr_par ^= 1;
-        if constexpr (sizeof(S) == 2)
-            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, true>, grid, 128, 0, st, d)
-                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, true>, grid, 128, 0, st, d);
+        if constexpr (sizeof(S) == 2) {
+            if (a.dyn_ns == 1)
+                return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, 1>, grid, 128, 0, st, d)
+                            : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, 1>, grid, 128, 0, st, d);
+            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, DYN_STRIPES>, grid, 128, 0, st, d)
+                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, DYN_STRIPES>, grid, 128, 0, st, d);
+        }
         else
             return fuse ? launch_pdl(k_step<S, LAW, VEC, true, false, false, true>, grid, 128, 0, st, d)
                         : launch_pdl(k_step<S, LAW, VEC, false, false, false, true>, grid, 128, 0, st, d);

@@ -273,19 +273,61 @@ def test_page_locked_host_arrays_give_the_same_results(lbm, storage):
         assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
 
 
+@pytest.mark.parametrize("yper", [False, True])
+def test_banded_host_init_equals_device_init(lbm, yper):
+    """lbm_init copies a large host state in row bands, each band's
+    initialization starting once the rows its stencils reach have arrived
+    (periodic rows: the first band last). The state equals, bit for bit, that
+    of lbm_init_device on the whole state already on the device, with and
+    without u0, on a lattice above the banding threshold whose row count is
+    not a multiple of the band count."""
+    import torch
+
+    nx, ny = 1100, 1203  # 6 x 8 B x 1.32 M nodes = 64 MB and more
+    U0 = smooth_field(nx, ny, seed=21, amp=0.04, periodic=yper)
+    u0 = 0.01 * smooth_field(nx, ny, seed=22)[:2]
+    out = []
+    for route in ("host", "device"):
+        for with_u0 in (False, True):
+            L = make(lbm, nx, ny, storage=1, omega=1.9)
+            if not yper:
+                lbm.lbm_set_boundary(L.ctx, lbm.LBM_EDGE_BOTTOM, lbm.LBM_BC_VELOCITY)
+                lbm.lbm_set_boundary(L.ctx, lbm.LBM_EDGE_TOP, lbm.LBM_BC_TRACTION, (0.02, 0.01))
+            uu = u0 if with_u0 else None
+            if route == "host":
+                lbm.lbm_init(L.ctx, torch.from_numpy(U0).pin_memory().numpy(), uu, 2)
+            else:
+                lbm.lbm_init_device(L.ctx, torch.from_numpy(U0).cuda(),
+                                    None if uu is None else torch.from_numpy(uu).cuda(), 2)
+            lbm.lbm_step(L.ctx, 2)
+            U, P, _ = lbm.lbm_read_state(L.ctx)
+            out.append((U, P, lbm.lbm_read_displacement(L.ctx)))
+            L.close()
+    for x, y in zip(out[:2], out[2:]):
+        for a, b in zip(x, y):
+            assert np.all(np.isfinite(a))
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
 @pytest.mark.parametrize("storage", [0, 1, 2])
 def test_dynamic_and_static_task_order_give_the_same_bits(lbm, storage, monkeypatch):
     """The step kernels take their tasks in static grid-stride order or
-    claim them dynamically from a device counter (LBM_DYN=0 / 1 force one;
-    otherwise the first lbm_step times both); a node's update does not
-    depend on which warp runs it, so both orders give the same bits, over
-    several steps (each dynamic launch uses the counter the previous one
-    zeroed) and with the variant choice's trial launches in between."""
+    claim them dynamically from device counters (LBM_DYN=0 / 1 force one,
+    LBM_DYN_STRIPES=1 / 4 the number of counters; otherwise the first
+    lbm_step times the variants); a node's update does not depend on which
+    warp runs it, so every order gives the same bits, over several steps
+    (each dynamic launch uses the counter set the previous one zeroed) and
+    with the variant choice's trial launches in between."""
     nx, ny = 300, 41
     U0 = smooth_field(nx, ny, seed=12, amp=0.04, periodic=False)
+    runs = [("0", None), ("1", "4")] + ([("1", "1")] if storage >= 2 else [])
     res = []
-    for dyn in ("1", "0"):
+    for dyn, ns in runs:
         monkeypatch.setenv("LBM_DYN", dyn)
+        if ns is None:
+            monkeypatch.delenv("LBM_DYN_STRIPES", raising=False)
+        else:
+            monkeypatch.setenv("LBM_DYN_STRIPES", ns)
         L = make(lbm, nx, ny, storage=storage, omega=1.9)
         lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
         lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.02, 0.01))
@@ -293,10 +335,11 @@ def test_dynamic_and_static_task_order_give_the_same_bits(lbm, storage, monkeypa
         for n in (1, 2, 7):
             lbm.lbm_step(L.ctx, n)
         v = lbm.lbm_step_variant(L.ctx)
-        assert v["dynamic"] == int(dyn)
+        assert v["dynamic"] == (0 if ns is None else int(ns))
         assert v["staged"] in ((0, 1) if dyn == "0" and storage >= 2 else (0,))
         U, P, _ = lbm.lbm_read_state(L.ctx)
         res.append((U, P, lbm.lbm_read_displacement(L.ctx)))
         L.close()
-    for x, y in zip(*res):
-        assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+    for other in res[1:]:
+        for x, y in zip(res[0], other):
+            assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
