@@ -299,7 +299,8 @@ __device__ __forceinline__ void adj_finish(const AdjArgs<typename Prec<S>::R> &a
 // per SM), which cut the backward step by 3% against loading and summing
 // one component at a time. FP64 keeps the component-at-a-time order: its
 // loads would need twice the registers.
-template <typename S, int LAW, int VEC>
+// NS: 0 static task order, else dynamic claims over NS stripes (claim_tasks)
+template <typename S, int LAW, int VEC, int NS = 0>
 __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjArgs<typename Prec<S>::R> a)
 {
     constexpr bool EARLY = sizeof(S) == 4;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjAr
     const S *__restrict__ fin = static_cast<const S *>(a.fin);
     const S *__restrict__ ain = static_cast<const S *>(a.ain);
 
-    for (int task = gw; task < ntask; task += nw) {
+    auto body = [&](int task) {
         int y, seg;
         task_coords(task, nseg, ny, y, seg);
         const int x0 = seg * segw + lane * VEC;
@@ -436,6 +437,12 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1) k_adj(const AdjAr
             U[1][e] += a.hdtb2;
         }
         adj_finish<S, LAW, VEC>(a, y, x0, lane, U, h, mu, ub0, ub1, gm);
+    };
+    if constexpr (NS > 0) {
+        if (blockIdx.x == 0 && threadIdx.x < DYN_STRIPES) a.ctr_next[threadIdx.x * DYN_CTR_STRIDE] = 0u;
+        claim_tasks<NS>(a.ctr, ntask, lane, body);
+    } else {
+        for (int task = gw; task < ntask; task += nw) body(task);
     }
 }
 
@@ -650,6 +657,10 @@ static cudaError_t launch_adj_t(const void *args, int grid, cudaStream_t st)
 {
     using T = typename Prec<S>::R;
     const auto &a = *static_cast<const AdjArgs<T> *>(args);
+    if constexpr (sizeof(S) == 4) {
+        if (a.ctr && a.dyn_ns == 1) return launch_pdl(k_adj<S, LAW, adj_vec<S>(), 1>, grid, 128, 0, st, a);
+        if (a.ctr) return launch_pdl(k_adj<S, LAW, adj_vec<S>(), DYN_STRIPES>, grid, 128, 0, st, a);
+    }
     return launch_pdl(k_adj<S, LAW, adj_vec<S>()>, grid, 128, 0, st, a);
 }
 

@@ -169,6 +169,10 @@ struct AdjArgs {
     T one_m_omega, wq, wi2c, dtT;  // 1 - w, w/4, w/(2c), dt
     T hdtb1, hdtb2, lam_ratio;
     double wi2c_d;
+    // dynamic task claims (claim_tasks, as the step kernels): this launch's
+    // counter set and the one it zeroes for the next, or nullptr (static)
+    unsigned *ctr, *ctr_next;
+    int dyn_ns;         // stripes of the claims (1 or DYN_STRIPES) when ctr is set
 };
 struct RecordArgs {
     const void *f;

@@ -161,6 +161,22 @@ def test_checkpoint_interval_does_not_change_the_gradient(lbm, storage):
         assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), K
 
 
+@pytest.mark.parametrize("order", ["1", "4"])
+def test_dynamic_task_order_does_not_change_the_gradient(lbm, monkeypatch, order):
+    """The FP32 adjoint kernel in dynamic task order (LBM_ADJ_DYN: one
+    counter or four stripes) gives the gradient of the static order bit for
+    bit, with and without checkpointing (the side stream's recomputation in
+    between the adjoint launches)."""
+    w = small_workload(nx=300, ny=37, steps=45)
+    for K in (1, 0):
+        monkeypatch.setenv("LBM_ADJ_DYN", "0")
+        ref = gpu_gradients(lbm, w, F32, checkpoint_every=K)
+        monkeypatch.setenv("LBM_ADJ_DYN", order)
+        got = gpu_gradients(lbm, w, F32, checkpoint_every=K)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), K
+
+
 def test_gradient_matches_central_differences_of_the_gpu_forward(lbm):
     import torch
 
