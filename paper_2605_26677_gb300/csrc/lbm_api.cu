@@ -943,14 +943,26 @@ lbm_status lbm_init(lbm_ctx *c, const double *U0, const double *u0, int32_t orde
     if (s != LBM_OK) return s;
     CK(c, cudaSetDevice(c->cfg.device));
     const size_t N = (size_t)c->L.nx * c->L.ny;
-    double *dU = nullptr, *du = nullptr;
-    CK(c, cudaMallocAsync((void **)&dU, 6 * N * sizeof(double), c->st));
-    cudaError_t e = u0 ? cudaMallocAsync((void **)&du, 2 * N * sizeof(double), c->st) : cudaSuccess;
+    // The copied state is staged in the second population buffer: the
+    // initialization writes f[0] and the first step overwrites f[1], and its
+    // 24 planes hold U0's 6 N doubles in every storage type (u0's 2 N too,
+    // except with 16-bit storage, where u0 gets an allocation of its own).
+    const size_t fbytes = (size_t)24 * c->L.plane * c->eb;
+    double *dU = static_cast<double *>(c->f[1]), *du = nullptr;
+    bool du_owned = false;
+    cudaError_t e = cudaSuccess;
+    if (u0) {
+        if (8 * N * sizeof(double) <= fbytes) {
+            du = dU + 6 * N;
+        } else {
+            e = cudaMallocAsync((void **)&du, 2 * N * sizeof(double), c->st);
+            du_owned = e == cudaSuccess;
+        }
+    }
     if (e == cudaSuccess) s = init_from_host(c, U0, u0, order, dU, du);
     if (s != LBM_OK) cudaStreamSynchronize(c->st_copy ? c->st_copy : c->st);  // copies still in flight
-    cudaFreeAsync(dU, c->st);
-    if (du) cudaFreeAsync(du, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "allocating the initial state");
+    if (du_owned) cudaFreeAsync(du, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "allocating the initial displacement");
     if (s != LBM_OK) return s;
     return sync_status(c);
 }
