@@ -195,16 +195,17 @@ lbm_status lbm_init(lbm_ctx *ctx, const double *U0, const double *u0, int32_t or
 lbm_status lbm_init_device(lbm_ctx *ctx, const double *U0_dev, const double *u0_dev, int32_t order);
 
 /* Advance nsteps >= 0 time steps (Sec. 3.7), then wait and return the
- * latched device status. With uniform material and the node form of F^b,
- * the context's first call with nsteps > 0 (after its first lbm_init or
- * lbm_init_device) first times the step-launch variants, which give
+ * latched device status. In the node form of F^b, the context's first call
+ * with nsteps > 0 after its first lbm_init or lbm_init_device (or its first
+ * lbm_adjoint_forward) first times the step-launch variants, which give
  * identical results: the task order (static, or claimed dynamically from
- * device counters) and, with BF16 or FP16 storage, the register or the
- * shared-memory staged kernel; a few trial steps leave the state untouched,
- * and the fastest is kept for the context's life (the trials take a
- * u*-sized scratch allocation while they run). Until then, and for
- * lbm_step_async, the register kernel runs in static order. LBM_STEP16=regs
- * or staged and LBM_DYN=0 or 1 in the environment restrict the choice. */
+ * device counters) and, with BF16 or FP16 storage and uniform material, the
+ * register or the shared-memory staged kernel; a few trial steps leave the
+ * state untouched, and the fastest is kept for the context's life (the
+ * trials take a u*-sized scratch allocation while they run). Until then, and
+ * for lbm_step_async, the register kernel runs in static order.
+ * LBM_STEP16=regs or staged, LBM_DYN=0 or 1 and LBM_DYN_STRIPES=1 or 4 in the
+ * environment restrict the choice. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* As lbm_step without waiting; check later with lbm_sync. */

@@ -181,6 +181,7 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         s.fout = fout;
         s.ustar = nullptr;
         s.status = a->status_scr;
+        s.ctr2 = nullptr;  // static order (the reason is given in the FP32 branch)
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
         AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
     } else {
@@ -189,6 +190,9 @@ lbm_status recompute_step(lbm_adjoint *a, const void *fin, void *fout, long long
         s.fout = fout;
         s.ustar = nullptr;
         s.status = a->status_scr;
+        // static order: beside the adjoint kernel on the other stream, the
+        // recomputation in dynamic order slowed the backward pass by 2.5%
+        s.ctr2 = nullptr;
         for (int e = 0; e < 4; ++e) s.g[e] = ctx_time_factor(c, e, n);
         AK(a, launch_step(c->cfg.storage, c->m.law, true, &s, c->grid_step, st));
     }
@@ -433,6 +437,10 @@ lbm_status forward_body(lbm_adjoint *a, const double *U0_dev, int32_t order, dou
     a->order = order;
     AK(a, cudaMemcpyAsync(a->U0, U0_dev, 6 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     s = ctx_refresh_ghosts(c);
+    if (s != LBM_OK) return afail(a, s, c->err);
+    // the forward and the recomputed segments step with the variant the
+    // context keeps for its lattice (chosen here if no lbm_step has yet)
+    s = ctx_tune_steps(c);
     if (s != LBM_OK) return afail(a, s, c->err);
     const long long n0 = c->step;  // 0 after init
     // Each step writes its state straight into its checkpoint buffer when it

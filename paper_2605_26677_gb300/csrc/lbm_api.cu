@@ -814,10 +814,11 @@ static lbm_status init_from_host(lbm_ctx *c, const double *U0, const double *u0,
 // context's life. The trials read the current buffer, whose ghost cells are
 // refreshed first exactly as the first step would, and write only the other
 // buffer, which the first real step overwrites; u* and the status word go to
-// scratch, so the state is untouched. LBM_STEP16 and LBM_DYN in the
-// environment restrict the candidates; contexts with a material field or the
-// extrapolated F^b form, or without room for the scratch, keep the register
-// kernel in static order.
+// scratch, so the state is untouched. LBM_STEP16, LBM_DYN and
+// LBM_DYN_STRIPES in the environment restrict the candidates; contexts in
+// the extrapolated F^b form, or without room for the scratch, keep the
+// register kernel in static order, and contexts with a material field have
+// no staged kernel.
 } // extern "C"
 
 namespace {
@@ -830,10 +831,11 @@ struct StepVariant {
 template <typename T>
 lbm_status tune_step(lbm_ctx *c)
 {
-    if (c->cfg.fb_mode != LBM_FB_NODE || c->d_muplane) return LBM_OK;
+    if (c->cfg.fb_mode != LBM_FB_NODE) return LBM_OK;
     std::vector<StepVariant> cand;
     const int env16 = tlv::step16_env_choice(), envdyn = tlv::dyn_env_choice(), envns = tlv::stripes_env_choice();
-    for (int k16 = 0; k16 < (c->eb == 2 ? 2 : 1); ++k16)
+    // the staged kernel has no per-node-material form
+    for (int k16 = 0; k16 < (c->eb == 2 && !c->d_muplane ? 2 : 1); ++k16)
         for (int d : {0, DYN_STRIPES, 1}) {
             if (d == 1 && (c->eb != 2 || DYN_STRIPES == 1)) continue;  // one counter: 16-bit kernels only
             if (k16 == 1 && d != 0) continue;                         // the staged kernel keeps static order
@@ -916,6 +918,17 @@ lbm_status tune_step(lbm_ctx *c)
 
 } // namespace
 
+lbm_status tlv::ctx_tune_steps(lbm_ctx *c)
+{
+    if (!c->initialized || !c->tune_pending) return LBM_OK;
+    lbm_status s = check_edges(c);
+    if (s == LBM_OK) s = (c->eb == 8) ? tune_step<double>(c) : tune_step<float>(c);
+    if (s != LBM_OK) return s;
+    c->tune_pending = false;
+    return LBM_OK;
+}
+
+
 extern "C" {
 
 static lbm_status init_checks(lbm_ctx *c, const void *U0, int32_t order)
@@ -989,13 +1002,11 @@ lbm_status lbm_step_async(lbm_ctx *c, int64_t nsteps)
 
 lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
 {
-    if (c && c->initialized && c->tune_pending && nsteps > 0) {
+    if (c && nsteps > 0) {
         // the context's first synchronising step picks the step-launch
         // variant for the lattice (tune_step)
-        lbm_status s = check_edges(c);
-        if (s == LBM_OK) s = (c->eb == 8) ? tune_step<double>(c) : tune_step<float>(c);
+        lbm_status s = tlv::ctx_tune_steps(c);
         if (s != LBM_OK) return s;
-        c->tune_pending = false;
     }
     lbm_status s = lbm_step_async(c, nsteps);
     if (s != LBM_OK) return s;

@@ -360,10 +360,12 @@ __device__ __forceinline__ void piola_ofs(R G11, R G12, R G21, R G22, const LawP
             a = R(0.5) * lam * dJ * (R(2) + dJ);
         else
             a = lam * log1p(dJ);
-        P11 = (mu * (G11 - G22 + dJ * (R(1) + G11)) + a * (R(1) + G22)) * invJ;
-        P12 = (mu * (G12 * J + G21) - a * G21) * invJ;
-        P21 = (mu * (G21 * J + G12) - a * G12) * invJ;
-        P22 = (mu * (G22 - G11 + dJ * (R(1) + G22)) + a * (R(1) + G11)) * invJ;
+        // mu / J and a / J formed once: P = (mu/J)(J F - cof F) + (a/J) cof F
+        const R mJ = mu * invJ, aJ = a * invJ;
+        P11 = mJ * (G11 - G22 + dJ * (R(1) + G11)) + aJ * (R(1) + G22);
+        P12 = mJ * (G12 * J + G21) - aJ * G21;
+        P21 = mJ * (G21 * J + G12) - aJ * G12;
+        P22 = mJ * (G22 - G11 + dJ * (R(1) + G22)) + aJ * (R(1) + G11);
     }
 }
 

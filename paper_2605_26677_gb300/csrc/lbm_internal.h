@@ -221,6 +221,9 @@ lbm_status ctx_ready(lbm_ctx *c);                 // initialized, edges consiste
 lbm_status ctx_refresh_ghosts(lbm_ctx *c);        // rebuild stale ghost cells (stream-ordered)
 template <typename T>
 StepArgs<T> ctx_step_args(const lbm_ctx *c, int cur);  // arguments of the step that reads f[cur]
+// the first synchronising step of an initialized context times the
+// step-launch variants on its lattice and keeps the fastest (no-op later)
+lbm_status ctx_tune_steps(lbm_ctx *c);
 double ctx_time_factor(const lbm_ctx *c, int e, long long step);  // g of edge e for the step from f*^step
 
 // lbm_batch_k32.cu / lbm_batch_k16.cu: batched step kernel for (law, nodes

@@ -114,56 +114,62 @@ __global__ void __launch_bounds__(128) k_ghosts(const EdgeArgs a)
 }
 
 // ---------------------------------------------------------------- launchers
+// One launch of the register step kernel with its variant fixed at compile
+// time: fused ghost writes, per-node material (MATF), no u* update (NOQ:
+// the adjoint's recomputed steps), and the task order (NS = 0 static, else
+// dynamic claims over NS stripes).
+template <typename S, int LAW, bool MATF, bool NOQ, int NS>
+static cudaError_t launch_step_v(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
+{
+    if constexpr (sizeof(S) == 2) {
+        static_assert(!NOQ, "the 16-bit kernels always update u*");
+        return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, MATF, NS>, grid, 128, 0, st, a)
+                    : launch_pdl(k_step16<S, LAW, STEP16_V, false, MATF, NS>, grid, 128, 0, st, a);
+    } else {
+        static_assert(NS == 0 || NS == DYN_STRIPES, "FP32 and FP64 kernels claim over DYN_STRIPES stripes");
+        constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors (unpacked kernels)
+        return fuse ? launch_pdl(k_step<S, LAW, VEC, true, MATF, NOQ, NS != 0>, grid, 128, 0, st, a)
+                    : launch_pdl(k_step<S, LAW, VEC, false, MATF, NOQ, NS != 0>, grid, 128, 0, st, a);
+    }
+}
+
+template <typename S, int LAW, bool MATF, bool NOQ>
+static cudaError_t launch_step_o(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
+{
+    if (!a.ctr2) return launch_step_v<S, LAW, MATF, NOQ, 0>(a, fuse, grid, st);
+    // dynamic task claims: this launch takes the counter set the previous
+    // dynamic launch zeroed (only dynamic launches touch the sets)
+    StepArgs<typename Prec<S>::R> d = a;
+    d.ctr = a.ctr2 + *a.ctr_par * DYN_SET_WORDS;
+    d.ctr_next = a.ctr2 + (*a.ctr_par ^ 1) * DYN_SET_WORDS;
+    *a.ctr_par ^= 1;
+    if constexpr (sizeof(S) == 2)
+        if (a.dyn_ns == 1) return launch_step_v<S, LAW, MATF, NOQ, 1>(d, fuse, grid, st);
+    return launch_step_v<S, LAW, MATF, NOQ, DYN_STRIPES>(d, fuse, grid, st);
+}
+
 template <typename S, int LAW>
 static cudaError_t launch_step_t(const StepArgs<typename Prec<S>::R> &a, bool fuse, int grid, cudaStream_t st)
 {
-    constexpr int VEC = 16 / sizeof(S);  // 16-byte vectors (unpacked kernels)
     if (a.mufield) {
         // per-node material: SVK / NH / log-NH; the 16-bit formats on the register kernel
         if constexpr (LAW > LAW_LOGNH) {
             return cudaErrorNotSupported;
         } else if constexpr (sizeof(S) == 2) {
             if (!a.ustar) return cudaErrorInvalidValue;
-            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, true>, grid, 128, 0, st, a)
-                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, true>, grid, 128, 0, st, a);
+            return launch_step_o<S, LAW, true, false>(a, fuse, grid, st);
         } else {
             // without u*: a step recomputed only for its populations (the
             // adjoint's checkpoint segments), 32 bytes per node less
-            if (!a.ustar)
-                return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true, true>, grid, 128, 0, st, a)
-                            : launch_pdl(k_step<S, LAW, VEC, false, true, true>, grid, 128, 0, st, a);
-            return fuse ? launch_pdl(k_step<S, LAW, VEC, true, true>, grid, 128, 0, st, a)
-                        : launch_pdl(k_step<S, LAW, VEC, false, true>, grid, 128, 0, st, a);
+            if (!a.ustar) return launch_step_o<S, LAW, true, true>(a, fuse, grid, st);
+            return launch_step_o<S, LAW, true, false>(a, fuse, grid, st);
         }
     }
     if constexpr (sizeof(S) == 2) {
         cudaError_t e;
         if (launch_step16_staged<S, LAW>(a, fuse, grid, st, e)) return e;
     }
-    if (a.ctr2) {
-        // dynamic task claims: this launch takes the counter the previous
-        // dynamic launch zeroed (only dynamic launches touch the pair)
-        StepArgs<typename Prec<S>::R> d = a;
-        d.ctr = a.ctr2 + *a.ctr_par * DYN_SET_WORDS;
-        d.ctr_next = a.ctr2 + (*a.ctr_par ^ 1) * DYN_SET_WORDS;
-        *a.ctr_par ^= 1;
-        if constexpr (sizeof(S) == 2) {
-            if (a.dyn_ns == 1)
-                return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, 1>, grid, 128, 0, st, d)
-                            : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, 1>, grid, 128, 0, st, d);
-            return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true, false, DYN_STRIPES>, grid, 128, 0, st, d)
-                        : launch_pdl(k_step16<S, LAW, STEP16_V, false, false, DYN_STRIPES>, grid, 128, 0, st, d);
-        }
-        else
-            return fuse ? launch_pdl(k_step<S, LAW, VEC, true, false, false, true>, grid, 128, 0, st, d)
-                        : launch_pdl(k_step<S, LAW, VEC, false, false, false, true>, grid, 128, 0, st, d);
-    }
-    if constexpr (sizeof(S) == 2)
-        return fuse ? launch_pdl(k_step16<S, LAW, STEP16_V, true>, grid, 128, 0, st, a)
-                    : launch_pdl(k_step16<S, LAW, STEP16_V, false>, grid, 128, 0, st, a);
-    else
-        return fuse ? launch_pdl(k_step<S, LAW, VEC, true>, grid, 128, 0, st, a)
-                    : launch_pdl(k_step<S, LAW, VEC, false>, grid, 128, 0, st, a);
+    return launch_step_o<S, LAW, false, false>(a, fuse, grid, st);
 }
 
 template <typename S>

@@ -343,3 +343,33 @@ def test_dynamic_and_static_task_order_give_the_same_bits(lbm, storage, monkeypa
     for other in res[1:]:
         for x, y in zip(res[0], other):
             assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_task_order_with_a_material_field(lbm, storage, monkeypatch):
+    """Per-node material (the adjoint's forward): static and dynamic task
+    order give the same bits, over several lbm_step calls and after the
+    variant choice's trial launches."""
+    nx, ny = 260, 33
+    U0 = smooth_field(nx, ny, seed=31, amp=0.03, periodic=False)
+    rng = np.random.default_rng(5)
+    mu = 0.5 * np.exp(0.2 * rng.standard_normal((ny, nx)))
+    res = []
+    for dyn in ("0", "1"):
+        monkeypatch.setenv("LBM_DYN", dyn)
+        monkeypatch.delenv("LBM_DYN_STRIPES", raising=False)
+        L = make(lbm, nx, ny, storage=storage, omega=1.9, c=6.0)
+        lbm.lbm_set_material_field(L.ctx, lbm.LBM_LAW_NH, mu, 2.0)
+        lbm.lbm_set_boundary(L.ctx, 0, lbm.LBM_BC_VELOCITY)
+        lbm.lbm_set_boundary(L.ctx, 1, lbm.LBM_BC_TRACTION, (0.01, 0.0))
+        lbm.lbm_init(L.ctx, U0)
+        for n in (1, 4, 6):
+            lbm.lbm_step(L.ctx, n)
+        v = lbm.lbm_step_variant(L.ctx)
+        assert (v["dynamic"] > 0) == (dyn == "1") and v["staged"] == 0
+        U, P, _ = lbm.lbm_read_state(L.ctx)
+        res.append((U, P, lbm.lbm_read_displacement(L.ctx)))
+        L.close()
+    for x, y in zip(*res):
+        assert np.all(np.isfinite(x))
+        assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
