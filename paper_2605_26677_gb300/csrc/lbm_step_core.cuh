@@ -15,6 +15,11 @@ struct alignas(sizeof(T) * N) Pack {
 
 #define FULL_MASK 0xffffffffu
 
+// x is NaN or infinite: all exponent bits set, tested on the integer pipe
+// (the FP64 pipe is the FP64 step's bottleneck)
+__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; }
+__device__ __forceinline__ bool nonfinite(float x) { return (__float_as_int(x) & 0x7f800000) == 0x7f800000; }
+
 // Dynamic task claims of one launch: the tasks [0, ntask) form NS contiguous
 // stripes, stripe j claimed through counter ctr[j * DYN_CTR_STRIDE] (zero
 // when the launch begins). A warp starts in the stripe of its global warp
@@ -108,7 +113,7 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, co
     piola_ofs<LAW, T>(U[2], U[3], U[4], U[5], m, P11, P12, P21, P22, dJ);
     if (real) {
         if (!(dJ > T(-1))) flags |= ST_BAD_J;
-        if (!(fabs(U[0]) + fabs(U[1]) + fabs(dJ) < T(INFINITY))) flags |= ST_NONFINITE;
+        if (nonfinite(U[0]) | nonfinite(U[1]) | nonfinite(dJ)) flags |= ST_NONFINITE;
     }
     v1 = U[0];
     v2 = U[1];
