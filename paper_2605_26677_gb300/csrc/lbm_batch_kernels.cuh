@@ -18,15 +18,49 @@
 
 namespace tlv {
 
+// Side-edge queue of one warp (unpacked kernels): XQ_CAP entries of
+// (x, y, member); a task adds at most two.
+constexpr int XQ_CAP = 64;
+
 template <typename S, int LAW, int V, bool PACKED>
-__device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
+__device__ __forceinline__ void batch_loop(const BatchList &b, int *off, int *xq)
 {
     using T = typename Prec<S>::R;
+    constexpr bool XQ = !PACKED;
     for (int i = threadIdx.x; i <= b.n; i += blockDim.x) off[i] = b.off[i];
     __syncthreads();
     const StepArgs<T> *args = static_cast<const StepArgs<T> *>(b.args);
     const int lane = threadIdx.x & 31;
     const int ntask = off[b.n];
+    int *qx = xq + (threadIdx.x >> 5) * 3 * XQ_CAP, *qy = qx + XQ_CAP, *qm = qy + XQ_CAP;
+    int qn = 0;  // queued side-edge nodes of this warp (warp-uniform)
+    // every lane of the warp takes one queued node (up to 32), then the rest
+    // moves to the front of the queue
+    auto flush = [&]() {
+        __syncwarp();  // the queued nodes' stores, made by this warp's lanes, are visible
+        const int nproc = qn < 32 ? qn : 32;
+        if (lane < nproc) {
+            const StepArgs<T> &a = args[qm[lane]];
+            unsigned f = 0;
+            xedge_node<LAW, S>(a, qx[lane], qy[lane], f);
+            if (f) atomicOr(a.status, (int)f);
+        }
+        const int rest = qn - nproc;
+        int rx = 0, ry = 0, rm = 0;
+        if (lane < rest) {
+            rx = qx[nproc + lane];
+            ry = qy[nproc + lane];
+            rm = qm[nproc + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+            qx[lane] = rx;
+            qy[lane] = ry;
+            qm[lane] = rm;
+        }
+        __syncwarp();
+        qn = rest;
+    };
     int m = 0;
     auto run = [&](int task) {
         // a warp's tasks grow except when it wraps from the last stripe to
@@ -43,12 +77,26 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
         m = lo;
         const StepArgs<T> &a = args[m];
         unsigned flags = 0;
+        XPend xp{-1, 0};
         if constexpr (PACKED)
             step16_task<S, LAW, V, true>(a, task - off[m], lane, flags);
         else
-            step_task<S, LAW, V, true>(a, task - off[m], lane, flags);
+            step_task<S, LAW, V, true, false, false, XQ>(a, task - off[m], lane, flags, &xp);
         flags = __reduce_or_sync(FULL_MASK, flags);
         if (flags && lane == 0) atomicOr(a.status, (int)flags);
+        if constexpr (XQ) {
+            const unsigned bal = __ballot_sync(FULL_MASK, xp.x >= 0);
+            if (bal) {
+                if (xp.x >= 0) {
+                    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                    qx[pos] = xp.x;
+                    qy[pos] = xp.y;
+                    qm[pos] = m;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) flush();
+            }
+        }
     };
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b.ctr) {
@@ -56,6 +104,8 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
         // finish zeroes them for the next launch (every claim of the launch
         // has returned by then)
         claim_tasks<DYN_STRIPES>(b.ctr, ntask, lane, run);
+        if constexpr (XQ)
+            while (qn > 0) flush();
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -68,6 +118,8 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off)
     } else {
         const int nw = gridDim.x * (blockDim.x >> 5);
         for (int task = gw; task < ntask; task += nw) run(task);
+        if constexpr (XQ)
+            while (qn > 0) flush();
     }
 }
 
@@ -76,7 +128,8 @@ template <typename S, int LAW, int V>
 __global__ void __launch_bounds__(128) k_batch(const BatchList b)
 {
     extern __shared__ int off[];
-    batch_loop<S, LAW, V, false>(b, off);
+    __shared__ int xq[4 * 3 * XQ_CAP];  // four warps' side-edge queues
+    batch_loop<S, LAW, V, false>(b, off, xq);
 }
 
 // packed 16-bit vectors of 4 nodes (the single-lattice 16-bit kernel's form)
@@ -84,7 +137,7 @@ template <typename S, int LAW>
 __global__ void __launch_bounds__(128, 3) k_batch16(const BatchList b)
 {
     extern __shared__ int off[];
-    batch_loop<S, LAW, 4, true>(b, off);
+    batch_loop<S, LAW, 4, true>(b, off, nullptr);
 }
 
 // nodes per lane that the batched kernels are built for

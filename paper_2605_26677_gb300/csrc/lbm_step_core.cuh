@@ -147,7 +147,7 @@ __device__ __forceinline__ void collide_node(T f[4][6], const StepArgs<T> &a, co
 // row (plane 3, y = ny), left ghost column (plane 0, x = -1), right ghost
 // column (plane 2, x = nx), with the edge data of the step that will pull
 // these values.
-template <int LAW, typename S, typename T>
+template <int LAW, typename S, typename T, bool SKIP_X = false>
 __device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const StepArgs<T> &a, const LawP<T> &m,
                                             S *fout, unsigned &flags)
 {
@@ -176,9 +176,53 @@ __device__ __forceinline__ void node_ghosts(const T f[4][6], int x, int y, const
     if (a.kind[EDGE_LEFT] == BC_PERIODIC) {
         if (x == nx - 1) put(EDGE_LEFT, -1, y, f[0]);
         if (x == 0) put(EDGE_RIGHT, nx, y, f[2]);
-    } else {
+    } else if (!SKIP_X) {
         if (x == 0) rule(EDGE_LEFT, y, -1, y);
         if (x == nx - 1) rule(EDGE_RIGHT, y, nx, y);
+    }
+}
+
+// Deferred side-edge rules (XQ kernels): a node on a non-periodic x edge
+// outside the two edge rows is not handled by its own lane while the warp's
+// 31 other lanes wait; its coordinates go to the warp's queue in shared
+// memory, and once 32 have gathered every lane of the warp takes one
+// (xedge_flush). The rule reads the node's stored post-collision values, as
+// the inline rule does, so the ghost values are the same bits.
+struct XPend {
+    int x, y;  // the lane's pending node, x = -1 for none
+};
+
+template <int LAW, typename S, bool MATF = false>
+__device__ __forceinline__ void xedge_node(const StepArgs<typename Prec<S>::R> &a, int x, int y, unsigned &flags)
+{
+    using T = typename Prec<S>::R;
+    S *fout = static_cast<S *>(a.fout);
+    const long long row = (long long)(y + 1) * a.L.pitch + a.L.xoff + x;
+    T fq[4][6];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fq[q][k] = ld_r(fout[(q * 6 + k) * a.L.plane + row]);
+    LawP<T> m{a.lam, a.mu, a.p2, a.p3};
+    if (MATF) {
+        m.mu = a.mufield[(long long)y * a.L.upitch + x];
+        m.lam = a.lam_ratio * m.mu;
+    }
+    // an interior row: only the side-edge rules apply to the node
+    const int nx = a.L.nx;
+    const T *f0 = fq[0], *f1 = fq[1], *f2 = fq[2], *f3 = fq[3];
+    T U[6], out[6];
+    state_from_fstar(f0, f1, f2, f3, a.hdtb1, a.hdtb2, U);
+    for (int side = 0; side < 2; ++side) {
+        const int e = side == 0 ? EDGE_LEFT : EDGE_RIGHT;
+        if ((side == 0 && x != 0) || (side == 1 && x != nx - 1)) continue;
+        const double g = (a.gdev ? a.gdev[e] : a.g[e]) * (a.profile[e] ? a.profile[e][y] : 1.0);
+        const double val[2] = {a.value[e][0] * g, a.value[e][1] * g};
+        edge_ghost<LAW, T>(e, a.kind[e], fq[edge_dout(e)], U, val, a.c, m, out, flags);
+        S *dst = fout + (long long)(edge_dmiss(e) * 6) * a.L.plane + (long long)(y + 1) * a.L.pitch + a.L.xoff +
+                 (side == 0 ? -1 : nx);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[k * a.L.plane] = to_store<S>(out[k]);
     }
 }
 
@@ -201,14 +245,23 @@ __device__ __forceinline__ void task_coords(int task, int nseg, int ny, int &y, 
 // back by the same thread), so the edge work never adds to the register peak
 // of the streaming loop, and it sees exactly the values the ghost-refresh
 // kernel would read.
-template <int LAW, typename S, int VEC, bool MATF = false>
+template <int LAW, typename S, int VEC, bool MATF = false, bool XQ = false>
 __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> &a, S *fout, long long row, int x0,
-                                            int y, unsigned &flags)
+                                            int y, unsigned &flags, XPend *xp = nullptr)
 {
     using T = typename Prec<S>::R;
     const int nx = a.L.nx, ny = a.L.ny;
     const bool edge_row = (y == 0 || y == ny - 1);
     if (!edge_row && x0 != 0 && !(x0 <= nx - 1 && nx - 1 < x0 + VEC)) return;
+    if constexpr (XQ) {
+        // one side-edge node of an interior row is deferred to the warp's
+        // queue; a lane holding both side nodes (nx <= VEC) keeps them
+        if (!edge_row && a.kind[EDGE_LEFT] != BC_PERIODIC && !(x0 == 0 && nx - 1 < x0 + VEC)) {
+            xp->x = (x0 == 0) ? 0 : nx - 1;
+            xp->y = y;
+            return;
+        }
+    }
 #pragma unroll 1
     for (int e = 0; e < VEC; ++e) {
         const int x = x0 + e;
@@ -232,9 +285,9 @@ __device__ __forceinline__ void lane_ghosts(const StepArgs<typename Prec<S>::R> 
 // One (row, segment) task of lattice `a`, executed by a whole warp.
 // NOQ: no displacement quadrature (states recomputed only for their
 // populations, as the adjoint's checkpoint segments are).
-template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false>
+template <typename S, int LAW, int VEC, bool FUSE, bool MATF = false, bool NOQ = false, bool XQ = false>
 __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a, int task, int lane,
-                                          unsigned &flags)
+                                          unsigned &flags, XPend *xp = nullptr)
 {
     using T = typename Prec<S>::R;  // compute type
     using PK = Pack<S, VEC>;        // stored vector
@@ -332,7 +385,7 @@ __device__ __forceinline__ void step_task(const StepArgs<typename Prec<S>::R> &a
                     *reinterpret_cast<PD *>(a.ustar + c * a.L.uplane + urow) = u;
                 }
             }
-            if (FUSE) lane_ghosts<LAW, S, VEC, MATF>(a, fout, row, x0, y, flags);
+            if (FUSE) lane_ghosts<LAW, S, VEC, MATF, XQ>(a, fout, row, x0, y, flags, xp);
         }
     }
 }
