@@ -18,48 +18,22 @@
 
 namespace tlv {
 
-// Side-edge queue of one warp (unpacked kernels): XQ_CAP entries of
-// (x, y, member); a task adds at most two.
-constexpr int XQ_CAP = 64;
-
 template <typename S, int LAW, int V, bool PACKED>
 __device__ __forceinline__ void batch_loop(const BatchList &b, int *off, int *xq)
 {
     using T = typename Prec<S>::R;
-    constexpr bool XQ = !PACKED;
+    constexpr bool XQ = !PACKED;  // side-edge rules deferred (unpacked kernels)
     for (int i = threadIdx.x; i <= b.n; i += blockDim.x) off[i] = b.off[i];
     __syncthreads();
     const StepArgs<T> *args = static_cast<const StepArgs<T> *>(b.args);
     const int lane = threadIdx.x & 31;
     const int ntask = off[b.n];
-    int *qx = xq + (threadIdx.x >> 5) * 3 * XQ_CAP, *qy = qx + XQ_CAP, *qm = qy + XQ_CAP;
-    int qn = 0;  // queued side-edge nodes of this warp (warp-uniform)
-    // every lane of the warp takes one queued node (up to 32), then the rest
-    // moves to the front of the queue
-    auto flush = [&]() {
-        __syncwarp();  // the queued nodes' stores, made by this warp's lanes, are visible
-        const int nproc = qn < 32 ? qn : 32;
-        if (lane < nproc) {
-            const StepArgs<T> &a = args[qm[lane]];
-            unsigned f = 0;
-            xedge_node<LAW, S>(a, qx[lane], qy[lane], f);
-            if (f) atomicOr(a.status, (int)f);
-        }
-        const int rest = qn - nproc;
-        int rx = 0, ry = 0, rm = 0;
-        if (lane < rest) {
-            rx = qx[nproc + lane];
-            ry = qy[nproc + lane];
-            rm = qm[nproc + lane];
-        }
-        __syncwarp();
-        if (lane < rest) {
-            qx[lane] = rx;
-            qy[lane] = ry;
-            qm[lane] = rm;
-        }
-        __syncwarp();
-        qn = rest;
+    XQueue q = XQ ? xq_make(xq) : XQueue{nullptr, nullptr, nullptr, 0};
+    auto proc = [&](int x, int y, int mm) {
+        const StepArgs<T> &a = args[mm];
+        unsigned f = 0;
+        xedge_node<LAW, S>(a, x, y, f);
+        if (f) atomicOr(a.status, (int)f);
     };
     int m = 0;
     auto run = [&](int task) {
@@ -84,19 +58,7 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off, int *xq
             step_task<S, LAW, V, true, false, false, XQ>(a, task - off[m], lane, flags, &xp);
         flags = __reduce_or_sync(FULL_MASK, flags);
         if (flags && lane == 0) atomicOr(a.status, (int)flags);
-        if constexpr (XQ) {
-            const unsigned bal = __ballot_sync(FULL_MASK, xp.x >= 0);
-            if (bal) {
-                if (xp.x >= 0) {
-                    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                    qx[pos] = xp.x;
-                    qy[pos] = xp.y;
-                    qm[pos] = m;
-                }
-                qn += __popc(bal);
-                if (qn >= 32) flush();
-            }
-        }
+        if constexpr (XQ) xq_push(q, xp, m, lane, proc);
     };
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b.ctr) {
@@ -105,7 +67,7 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off, int *xq
         // has returned by then)
         claim_tasks<DYN_STRIPES>(b.ctr, ntask, lane, run);
         if constexpr (XQ)
-            while (qn > 0) flush();
+            while (q.n > 0) xq_flush(q, lane, proc);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -119,7 +81,7 @@ __device__ __forceinline__ void batch_loop(const BatchList &b, int *off, int *xq
         const int nw = gridDim.x * (blockDim.x >> 5);
         for (int task = gw; task < ntask; task += nw) run(task);
         if constexpr (XQ)
-            while (qn > 0) flush();
+            while (q.n > 0) xq_flush(q, lane, proc);
     }
 }
 

@@ -192,6 +192,61 @@ struct XPend {
     int x, y;  // the lane's pending node, x = -1 for none
 };
 
+// The queue of one warp: XQ_CAP entries (x, y, member) in shared memory; a
+// task adds at most two, and 32 are processed as soon as they are queued.
+constexpr int XQ_CAP = 64;
+struct XQueue {
+    int *qx, *qy, *qm;
+    int n;  // warp-uniform
+};
+
+__device__ __forceinline__ XQueue xq_make(int *base)
+{
+    int *qx = base + (threadIdx.x >> 5) * 3 * XQ_CAP;
+    return XQueue{qx, qx + XQ_CAP, qx + 2 * XQ_CAP, 0};
+}
+
+// up to 32 queued nodes, one per lane (proc(x, y, m)); the rest moves to the
+// front of the queue
+template <typename Proc>
+__device__ __forceinline__ void xq_flush(XQueue &q, int lane, Proc &&proc)
+{
+    __syncwarp();  // the queued nodes' stores, made by this warp's lanes, are visible
+    const int nproc = q.n < 32 ? q.n : 32;
+    if (lane < nproc) proc(q.qx[lane], q.qy[lane], q.qm[lane]);
+    const int rest = q.n - nproc;
+    int rx = 0, ry = 0, rm = 0;
+    if (lane < rest) {
+        rx = q.qx[nproc + lane];
+        ry = q.qy[nproc + lane];
+        rm = q.qm[nproc + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        q.qx[lane] = rx;
+        q.qy[lane] = ry;
+        q.qm[lane] = rm;
+    }
+    __syncwarp();
+    q.n = rest;
+}
+
+// the lanes' pending nodes of one task (member m) into the queue
+template <typename Proc>
+__device__ __forceinline__ void xq_push(XQueue &q, const XPend &xp, int m, int lane, Proc &&proc)
+{
+    const unsigned bal = __ballot_sync(0xffffffffu, xp.x >= 0);
+    if (!bal) return;
+    if (xp.x >= 0) {
+        const int pos = q.n + __popc(bal & ((1u << lane) - 1u));
+        q.qx[pos] = xp.x;
+        q.qy[pos] = xp.y;
+        q.qm[pos] = m;
+    }
+    q.n += __popc(bal);
+    if (q.n >= 32) xq_flush(q, lane, proc);
+}
+
 template <int LAW, typename S, bool MATF = false>
 __device__ __forceinline__ void xedge_node(const StepArgs<typename Prec<S>::R> &a, int x, int y, unsigned &flags)
 {
