@@ -341,7 +341,10 @@ lbm_status lbm_batch_set_task_order(lbm_batch *b, int32_t size_class, int32_t dy
 
 /* Autotuner: for every size class that has members, times `reps` (>= 1)
  * launches of that class alone for each tile that exists, in each task order,
- * and keeps the fastest (tile, order). The trial launches write only the
+ * and keeps the fastest (tile, order); where a class other than the one with
+ * the most nodes chose dynamic order, it then times the whole batch with
+ * those orders and with static order for those classes, and keeps the
+ * faster. The trial launches write only the
  * members' second population buffer and scratch copies of the displacement
  * accumulator and status, so the members' states do not change. us (host,
  * optional) receives LBM_BATCH_CLASSES x 3 doubles: mean microseconds per

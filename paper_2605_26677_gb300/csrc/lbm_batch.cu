@@ -629,6 +629,35 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
     }
     const std::vector<lbm_ctx *> all = b->m;
     const int n_all = b->n;
+    // mean microseconds per step of the current tiles and orders on the
+    // members `ms` alone (trial launches: scratch u* and status)
+    auto trial = [&](const std::vector<lbm_ctx *> &ms, double &t_us) -> lbm_status {
+        b->m = ms;
+        b->n = (int)ms.size();
+        Plan p;
+        lbm_status r = make_plan(b, p);
+        p.timed = false;  // trials take the time factors of the current step from the host
+        if (r == LBM_OK) r = upload_plan(b, p, u_scratch, stat_scratch);
+        if (r == LBM_OK) r = ensure_side_streams(b, (int)p.groups.size());
+        float ms_ = 0.f;
+        if (r == LBM_OK) {
+            for (int i = 0; i < 2 && r == LBM_OK; ++i) r = enqueue_step(b, p, 0);  // warm-up
+            if (r == LBM_OK) cudaEventRecord(t0, b->st);
+            for (int i = 0; i < reps && r == LBM_OK; ++i) r = enqueue_step(b, p, 0);
+            if (r == LBM_OK) {
+                cudaEventRecord(t1, b->st);
+                cudaError_t e = cudaEventSynchronize(t1);
+                if (e != cudaSuccess) r = bcuda(b, e, "cudaEventSynchronize");
+            }
+            if (r == LBM_OK) cudaEventElapsedTime(&ms_, t0, t1);
+        }
+        b->m = all;
+        b->n = n_all;
+        t_us = 1000.0 * ms_ / reps;
+        return r;
+    };
+    long long cls_nodes[NCLASS] = {};
+    for (lbm_ctx *c : all) cls_nodes[size_class(c->L.nx)] += (long long)c->L.nx * c->L.ny;
     for (int cls = 0; cls < NCLASS && s == LBM_OK; ++cls) {
         // the batch viewed as this class's members alone
         std::vector<lbm_ctx *> mine;
@@ -639,33 +668,13 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
         double best = 1e300;
         for (size_t ti = 0; ti < tiles.size() && s == LBM_OK; ++ti)
             for (int order = 0; order < 2 && s == LBM_OK; ++order) {
-                b->m = mine;
-                b->n = (int)mine.size();
                 b->vec[cls] = tiles[ti];
                 b->dyn[cls] = order;
-                Plan p;
-                s = make_plan(b, p);
-                p.timed = false;  // trials take the time factors of the current step from the host
-                if (s == LBM_OK) s = upload_plan(b, p, u_scratch, stat_scratch);
-                if (s == LBM_OK) s = ensure_side_streams(b, (int)p.groups.size());
-                float ms = 0.f;
-                if (s == LBM_OK) {
-                    for (int r = 0; r < 2 && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);  // warm-up
-                    if (s == LBM_OK) cudaEventRecord(t0, b->st);
-                    for (int r = 0; r < reps && s == LBM_OK; ++r) s = enqueue_step(b, p, 0);
-                    if (s == LBM_OK) {
-                        cudaEventRecord(t1, b->st);
-                        cudaError_t e = cudaEventSynchronize(t1);
-                        if (e != cudaSuccess) s = bcuda(b, e, "cudaEventSynchronize");
-                    }
-                    if (s == LBM_OK) cudaEventElapsedTime(&ms, t0, t1);
-                }
-                b->m = all;
-                b->n = n_all;
+                double t_us = 0.0;
+                s = trial(mine, t_us);
                 b->vec[cls] = keep;
                 b->dyn[cls] = keep_dyn;
                 if (s != LBM_OK) break;
-                const double t_us = 1000.0 * ms / reps;
                 if (us && (order == 0 || t_us < us[cls * 3 + ti])) us[cls * 3 + ti] = t_us;
                 if (t_us < best) {
                     best = t_us;
@@ -673,6 +682,39 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t reps, double *us)
                     chosen_dyn[cls] = order;
                 }
             }
+    }
+    // The orders were chosen one class at a time. Together, dynamic order in
+    // a smaller class can cost more than it saved alone (256 specimens:
+    // 0.897-0.899 of the copy bandwidth with classes 2 or 3 dynamic, 0.902
+    // with only the largest): the whole batch is timed with the chosen
+    // orders and with static order for every class but the one with the
+    // most nodes, and the faster is kept.
+    int big = 0;
+    for (int k = 1; k < NCLASS; ++k)
+        if (cls_nodes[k] > cls_nodes[big]) big = k;
+    bool small_dyn = false;
+    for (int k = 0; k < NCLASS; ++k)
+        if (k != big && cls_nodes[k] > 0 && chosen_dyn[k]) small_dyn = true;
+    if (s == LBM_OK && small_dyn) {
+        int keep_vec[NCLASS], keep_dyn[NCLASS];
+        for (int k = 0; k < NCLASS; ++k) {
+            keep_vec[k] = b->vec[k];
+            keep_dyn[k] = b->dyn[k];
+            b->vec[k] = chosen[k];
+            b->dyn[k] = chosen_dyn[k];
+        }
+        double t_chosen = 0.0, t_static = 0.0;
+        s = trial(all, t_chosen);
+        for (int k = 0; k < NCLASS; ++k)
+            if (k != big) b->dyn[k] = 0;
+        if (s == LBM_OK) s = trial(all, t_static);
+        for (int k = 0; k < NCLASS; ++k) {
+            b->vec[k] = keep_vec[k];
+            b->dyn[k] = keep_dyn[k];
+        }
+        if (s == LBM_OK && t_static < t_chosen)
+            for (int k = 0; k < NCLASS; ++k)
+                if (k != big) chosen_dyn[k] = 0;
     }
     b->m = all;
     b->n = n_all;
