@@ -13,7 +13,7 @@ Reported (one JSON line on rank 0):
   e2e       MLUPS through the public C ABI with host buffers: the initial
             state copied in from pinned memory and initialized, the steps,
             and the final state and displacement copied out, all inside the
-            timed region (with the time of each part; the median of three
+            timed region (with the time of each part; the median of five
             passes when --steps <= 200);
   roofline  the step kernel's algorithmic bytes per launch (224 B per node)
             over its mean launch duration in the timed region (CUDA events
@@ -261,8 +261,8 @@ def e2e_run(lbm, torch, w, U0, steps, warmup):
     `steps` steps, then lbm_read_state (U) and lbm_read_displacement into
     pinned host arrays, all inside the timed region; every call returns
     only after its work is done. Short runs (steps <= 200, where the host
-    copies weigh and single host-side delays of tens of ms occur) take the
-    median of three such passes, longer ones one pass. Returns (MLUPS, h2d
+    copies weigh and host-side delays of tens of ms hit some passes) take
+    the median of five such passes, longer ones one pass. Returns (MLUPS, h2d
     bytes, d2h bytes, the time of each part in ms of the pass taken, the
     total ms of every pass)."""
     U0p = torch.from_numpy(U0).pin_memory().numpy()
@@ -274,7 +274,7 @@ def e2e_run(lbm, torch, w, U0, steps, warmup):
     lbm.lbm_read_state(L.ctx, Uout, None, want_P=False)
     lbm.lbm_read_displacement(L.ctx, uout)
     passes = []
-    for _ in range(3 if steps <= 200 else 1):
+    for _ in range(5 if steps <= 200 else 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lbm.lbm_init(L.ctx, U0p, None, 2)
