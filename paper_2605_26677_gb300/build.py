@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUTDIR, "liblbm_gb300.so")
 SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_step_f64.cu", "lbm_step_f32.cu", "lbm_step_bf16.cu", "lbm_step_f16.cu",
-           "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_batch_k32.cu", "lbm_batch_k16.cu", "lbm_adjoint.cu",
+           "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_batch_k64.cu", "lbm_batch_k32.cu", "lbm_batch_k16.cu",
+           "lbm_batch_kf16.cu", "lbm_adjoint.cu",
            "lbm_adjoint_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -59,8 +59,12 @@ int default_tile(int storage, int cls)
 
 const void *kernel_for(int storage, int law, int vec)
 {
-    return (storage == STORE_F64 || storage == STORE_F32) ? batch_kernel_wide(storage, law, vec)
-                                                          : batch_kernel_16(storage, law, vec);
+    switch (storage) {
+    case STORE_F64: return batch_kernel_f64(law, vec);
+    case STORE_F32: return batch_kernel_f32(law, vec);
+    case STORE_BF16: return batch_kernel_bf16(law, vec);
+    default: return batch_kernel_f16(law, vec);
+    }
 }
 
 struct Group {

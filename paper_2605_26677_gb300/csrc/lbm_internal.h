@@ -228,7 +228,9 @@ double ctx_time_factor(const lbm_ctx *c, int e, long long step);  // g of edge e
 
 // lbm_batch_k32.cu / lbm_batch_k16.cu: batched step kernel for (law, nodes
 // per lane), or nullptr if that form is not built
-const void *batch_kernel_wide(int storage, int law, int vec);
-const void *batch_kernel_16(int storage, int law, int vec);
+const void *batch_kernel_f64(int law, int vec);
+const void *batch_kernel_f32(int law, int vec);
+const void *batch_kernel_bf16(int law, int vec);
+const void *batch_kernel_f16(int law, int vec);
 
 } // namespace tlv
